@@ -1,0 +1,221 @@
+/*
+ * cheesegpu.h -- C ABI of a GB300 (sm_103a) implementation of the Cheesemap
+ * neighbour-search hot path (arXiv 2502.11602): a uniform voxel grid over a
+ * point cloud, fixed-radius sphere / cube queries and exact k-NN.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Points and queries are float64 AoS arrays [n][3] (x, y, z) in device
+ *    memory unless a name says _host.  Neighbour ids are 0-based int32 ids in
+ *    the caller's original point order (batched indexes: ids into the
+ *    concatenated point array).
+ *  - Every call is ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls return as soon as the work is enqueued, except where a
+ *    comment says the call synchronises the stream.
+ *  - The caller owns every buffer it passes; the library never frees caller
+ *    memory.  An index owns its internal device buffers until
+ *    cg_index_free().  Internal buffers come from cudaMallocAsync on the
+ *    call's stream, or from the hook installed by cg_set_allocator().
+ *  - Every call returns a cg_status.  On an error nothing is written to the
+ *    caller's outputs except where stated, and cg_last_error() returns a
+ *    message for the calling thread.
+ *  - The neighbour sets are fixed by one predicate, evaluated in IEEE binary64
+ *    with round-to-nearest and no fused multiply-add:
+ *        dx = fl(p_x - c_x), dy, dz likewise;
+ *        sphere: fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) <= fl(r*r)
+ *        cube:   max(fl(dx*dx), fl(dy*dy), fl(dz*dz))  <= fl(r*r)
+ *    (the kernels of Section 2 / Section 3.4.1 of the paper, with "<=" as in
+ *    the candidate set of Section 3.4.2).  k-NN returns the first min(k, N)
+ *    points under the order (sphere value d2, original id).  Both precisions
+ *    below return exactly these sets.
+ */
+#ifndef CHEESEGPU_H_
+#define CHEESEGPU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CG_OK = 0,
+  CG_ERR_INVALID = 1,       /* bad argument (see each call)                      */
+  CG_ERR_OOM = 2,           /* device allocation failed                          */
+  CG_ERR_CUDA = 3,          /* a CUDA runtime call failed                        */
+  CG_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (no hang)           */
+  CG_ERR_OVERFLOW = 5,      /* an output capacity was too small                  */
+  CG_ERR_INTERNAL = 6,      /* a device-side consistency check failed            */
+  CG_ERR_UNIMPLEMENTED = 7
+} cg_status;
+
+/* Voxel storage flavours, Section 3.3: dense array over all voxels (3.3.1);
+   sparse map over non-empty voxels (3.3.2), here a sorted unique-key table
+   plus an open-addressing device hash; mixed z slices, each dense iff at
+   least 80 % of its voxels are non-empty, 2D = one slice (3.3.3). */
+typedef enum { CG_DENSE = 0, CG_SPARSE = 1, CG_MIXED = 2 } cg_flavor;
+
+/* Search kernels of Section 2: L2 ball and L-infinity ball (cube). */
+typedef enum { CG_SPHERE = 0, CG_CUBE = 1 } cg_kernel;
+
+/* Storage precision of the indexed coordinates.  CG_FP64 tests every
+   candidate in binary64.  CG_FP32_OFFSET stores fl32(fl64(p - O)) for a
+   per-tile origin O, tests candidates in binary32 and re-tests in binary64
+   every candidate whose binary32 value falls within a proven error bound of
+   r^2; the result sets are identical. */
+typedef enum { CG_FP64 = 0, CG_FP32_OFFSET = 1 } cg_precision;
+
+typedef struct cg_index* cg_index_t;
+
+/* Optional device-memory hook (e.g. a framework's caching allocator).
+   alloc returns NULL on failure; free receives the pointer and the stream
+   the allocation was made on. */
+typedef void* (*cg_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*cg_free_fn)(void* ptr, void* stream, void* user);
+
+/* Installs (or, with both NULL, removes) the allocation hook for buffers
+   made by later calls.  Not thread-safe against concurrent library calls. */
+cg_status cg_set_allocator(cg_alloc_fn alloc_fn, cg_free_fn free_fn, void* user);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* cg_last_error(void);
+
+/* Library version string. */
+const char* cg_version(void);
+
+/*
+ * cg_build -- index n points (Section 3: bounding box p-/p+ of Section 3.1,
+ * grid size n_a = floor((p+_a - p-_a)/s_a) + 1 of Eq. grid-size, voxel of a
+ * point floor((p_a - p-_a)/s_a) of Eq. chs-point-to-idcs with 0-based
+ * indices, global voxel index of Eqs. indices-to-global-2D/-3D, points
+ * reordered by voxel as in the "Reordering" remark of Section 3.5, with ties
+ * kept in ascending original id).
+ *
+ *  xyz_dev   device float64 [n][3]; read during the call only (copied).
+ *  n         number of points, 1 <= n < 2^31.
+ *  cell_xy   voxel size along x and y (> 0, finite).
+ *  cell_z    voxel size along z (> 0, finite); for 3D grids and for the
+ *            z slices of the mixed flavour (s_z of Section 3.3.3).
+ *  dim       2 (index x, y; z is not indexed) or 3.
+ *  flavor    storage flavour.   precision  coordinate precision.
+ *  out       receives the new index handle.
+ * Errors: CG_ERR_INVALID for n out of range, non-positive or non-finite cell
+ * sizes, dim not in {2, 3}, a non-finite coordinate, or more than 2^32 - 2
+ * voxels in the grid; CG_ERR_OOM.  The call synchronises `stream` (grid
+ * sizes depend on the data).
+ */
+cg_status cg_build(const double* xyz_dev, int64_t n, double cell_xy, double cell_z, int dim,
+                   cg_flavor flavor, cg_precision precision, void* stream, cg_index_t* out);
+
+/*
+ * cg_build_batched -- index T independent tiles in one index (each tile its
+ * own bounding box, origin, grid and cell size; voxel keys of different
+ * tiles never collide).  Queries against a batched index are per tile: see
+ * cg_query_all_points_batched.
+ *  xyz_dev       device float64 [N][3], tiles concatenated.
+ *  tile_offsets  HOST int64 [T+1], tile t owns points [off[t], off[t+1]).
+ *  T             number of tiles, >= 1; every tile non-empty.
+ *  cell_xy_host  HOST float64 [T] voxel size per tile (x, y and z).
+ * Same errors and synchronisation as cg_build.
+ */
+cg_status cg_build_batched(const double* xyz_dev, const int64_t* tile_offsets, int32_t T,
+                           const double* cell_xy_host, int dim, cg_flavor flavor,
+                           cg_precision precision, void* stream, cg_index_t* out);
+
+typedef struct {
+  int64_t n;            /* indexed points                                   */
+  int32_t dim, flavor, precision, ntiles;
+  int64_t ncell;        /* voxels of the grid(s), empty included             */
+  int64_t nonempty;     /* non-empty voxels                                  */
+  int64_t nslices;      /* z slices (mixed 3D), else 1 per tile              */
+  int64_t dense_slices; /* slices stored dense                               */
+  int64_t device_bytes; /* device memory held by the index                   */
+  double lo[3], hi[3];  /* bounding box of tile 0 (Section 3.1)              */
+  int64_t nc[3];        /* n_x, n_y, n_z of tile 0 (n_z = 1 in 2D)          */
+  double cell[3];       /* voxel size of tile 0                              */
+  double origin[3];     /* binary32 offset origin O of tile 0                */
+  double enc_err;       /* bound on |fl32(fl64(p-O)) - fl64(p-O)|, tile 0    */
+} cg_index_info_t;
+
+cg_status cg_index_info(cg_index_t index, cg_index_info_t* info);
+
+/* Synchronises `stream`, then returns (and clears) any device-side error
+   recorded by earlier calls on this index: CG_ERR_TIMEOUT (a bounded wait
+   gave up), CG_ERR_OVERFLOW, CG_ERR_INTERNAL (a consistency check failed;
+   the affected output was not written past its bounds), CG_ERR_INVALID (a
+   non-finite query coordinate).  CG_OK if none. */
+cg_status cg_index_status(cg_index_t index, void* stream);
+
+/* Releases the index (stream-ordered on the stream it was built on). */
+cg_status cg_index_free(cg_index_t index);
+
+/*
+ * cg_radius_count -- pass 1 of the two-pass kernel search (Algorithm 1 run
+ * for every query: voxel range of the kernel's bounding box, scan of the
+ * voxels' points, predicate).  Writes offsets[0..nq] = exclusive prefix sum
+ * of the per-query neighbour counts (offsets[0] = 0, offsets[nq] = total).
+ *  q_dev        device float64 [nq][3] query centres (any position).
+ *  nq           >= 0.  r > 0 finite.  kernel  CG_SPHERE or CG_CUBE.
+ *  offsets_dev  device int64 [nq+1], written.
+ *  total_host   if non-NULL receives the total; the call then synchronises.
+ * Queries keep an internal plan (query order, blocks) that cg_radius_fill
+ * reuses when it is given the same q_dev, nq, r and kernel next.
+ */
+cg_status cg_radius_count(cg_index_t index, const double* q_dev, int64_t nq, double r,
+                          cg_kernel kernel, int64_t* offsets_dev, int64_t* total_host,
+                          void* stream);
+
+/*
+ * cg_radius_fill -- pass 2: writes every query's neighbour ids at
+ * indices_dev[offsets[q] .. offsets[q+1]), each row ascending.
+ *  offsets_dev  as produced by cg_radius_count for the same arguments.
+ *  indices_dev  device int32 [offsets[nq]].
+ */
+cg_status cg_radius_fill(cg_index_t index, const double* q_dev, int64_t nq, double r,
+                         cg_kernel kernel, const int64_t* offsets_dev, int32_t* indices_dev,
+                         void* stream);
+
+/*
+ * cg_radius_search -- count + scan + fill with outputs allocated by the
+ * library (hook or cudaMallocAsync); the caller releases them with
+ * cg_free_device (or its own hook).  Synchronises the stream once (the
+ * total sizes the output).
+ */
+cg_status cg_radius_search(cg_index_t index, const double* q_dev, int64_t nq, double r,
+                           cg_kernel kernel, int64_t** offsets_dev, int32_t** indices_dev,
+                           int64_t* total, void* stream);
+
+/* Frees a buffer returned by cg_radius_search (stream-ordered). */
+cg_status cg_free_device(void* ptr, void* stream);
+
+/*
+ * Queries that are the indexed points themselves (every point a query, no
+ * copy of the queries): same outputs as the calls above with q = the points
+ * in original order, nq = n.
+ */
+cg_status cg_all_points_count(cg_index_t index, double r, cg_kernel kernel, int64_t* offsets_dev,
+                              int64_t* total_host, void* stream);
+cg_status cg_all_points_fill(cg_index_t index, double r, cg_kernel kernel,
+                             const int64_t* offsets_dev, int32_t* indices_dev, void* stream);
+
+/*
+ * cg_knn -- exact k nearest neighbours of every query (Algorithm 2's result:
+ * the k closest points; ring-by-ring expansion over the voxel grid with the
+ * visited region kept as an index box, the taboo box of Section 3.5).
+ *  k            1 <= k <= 64.
+ *  idx_dev      device int32 [nq][k]: ids ordered by (d2, id); -1 padding
+ *               when the index holds fewer than k points.
+ *  d2_dev       device float64 [nq][k] or NULL: the binary64 sphere value of
+ *               each neighbour (+inf for padding).
+ */
+cg_status cg_knn(cg_index_t index, const double* q_dev, int64_t nq, int32_t k, int32_t* idx_dev,
+                 double* d2_dev, void* stream);
+cg_status cg_all_points_knn(cg_index_t index, int32_t k, int32_t* idx_dev, double* d2_dev,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEESEGPU_H_ */

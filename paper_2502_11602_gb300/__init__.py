@@ -1,0 +1,264 @@
+"""cheesegpu: GB300 (sm_103a) Cheesemap neighbour search behind a C ABI.
+
+Thin Python binding over ``libcheesegpu.so`` (``include/cheesegpu.h``).  It
+only marshals arguments: torch tensors provide device memory and streams,
+every step of the build and of the queries runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+
+Functions with the C ABI's names (``cg_build``, ``cg_radius_count``, ...) take
+the same arguments as the C calls, with tensors for device pointers; the
+``Index`` class is a convenience wrapper around them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+DENSE, SPARSE, MIXED = 0, 1, 2
+SPHERE, CUBE = 0, 1
+FP64, FP32_OFFSET = 0, 1
+
+STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4: "CG_ERR_TIMEOUT",
+          5: "CG_ERR_OVERFLOW", 6: "CG_ERR_INTERNAL", 7: "CG_ERR_UNIMPLEMENTED"}
+
+EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_build", "cg_build_batched",
+           "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
+           "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
+           "cg_all_points_knn"]
+
+
+class CheeseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int32), ("flavor", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("ntiles", ctypes.c_int32), ("ncell", ctypes.c_int64),
+                ("nonempty", ctypes.c_int64), ("nslices", ctypes.c_int64),
+                ("dense_slices", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("nc", ctypes.c_int64 * 3),
+                ("cell", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
+                ("enc_err", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libcheesegpu.so (building it first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"cheesegpu library not found at {path}")
+        lib = ctypes.CDLL(path)
+        P, I64, I32, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int
+        sig = {
+            "cg_set_allocator": [P, P, P],
+            "cg_last_error": [],
+            "cg_version": [],
+            "cg_build": [P, I64, D, D, I, I, I, P, P],
+            "cg_build_batched": [P, P, I32, P, I, I, I, P, P],
+            "cg_index_info": [P, P],
+            "cg_index_free": [P],
+            "cg_index_status": [P, P],
+            "cg_radius_count": [P, P, I64, D, I, P, P, P],
+            "cg_radius_fill": [P, P, I64, D, I, P, P, P],
+            "cg_radius_search": [P, P, I64, D, I, P, P, P, P],
+            "cg_free_device": [P, P],
+            "cg_all_points_count": [P, D, I, P, P, P],
+            "cg_all_points_fill": [P, D, I, P, P, P],
+            "cg_knn": [P, P, I64, I32, P, P, P],
+            "cg_all_points_knn": [P, I32, P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("cg_last_error", "cg_version") else ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(code: int):
+    if code != 0:
+        msg = load().cg_last_error().decode()
+        raise CheeseError(code, msg)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _points(x: torch.Tensor) -> torch.Tensor:
+    if x.dtype != torch.float64 or x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError("points must be a float64 tensor of shape (n, 3)")
+    return x.contiguous()
+
+
+# ---------------------------------------------------------------- C ABI names
+
+
+def cg_version() -> str:
+    return load().cg_version().decode()
+
+
+def cg_build(xyz: torch.Tensor, cell_xy: float, cell_z: float | None = None, dim: int = 2,
+             flavor: int = DENSE, precision: int = FP32_OFFSET, stream=None) -> int:
+    xyz = _points(xyz)
+    h = ctypes.c_void_p()
+    _check(load().cg_build(_ptr(xyz), xyz.shape[0], float(cell_xy),
+                           float(cell_z if cell_z is not None else cell_xy), dim, flavor, precision,
+                           _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def cg_build_batched(xyz: torch.Tensor, tile_offsets, cells, dim: int = 2, flavor: int = DENSE,
+                     precision: int = FP32_OFFSET, stream=None) -> int:
+    import numpy as np
+    xyz = _points(xyz)
+    toff = np.ascontiguousarray(tile_offsets, dtype=np.int64)
+    cel = np.ascontiguousarray(cells, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load().cg_build_batched(_ptr(xyz), toff.ctypes.data, len(toff) - 1, cel.ctypes.data, dim,
+                                   flavor, precision, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def cg_index_info(h: int) -> dict:
+    info = IndexInfo()
+    _check(load().cg_index_info(h, ctypes.byref(info)))
+    return {f: (list(getattr(info, f)) if isinstance(getattr(info, f), ctypes.Array) else getattr(info, f))
+            for f, _ in IndexInfo._fields_}
+
+
+def cg_index_status(h: int, stream=None):
+    _check(load().cg_index_status(h, _stream(stream)))
+
+
+def cg_index_free(h: int):
+    _check(load().cg_index_free(h))
+
+
+def cg_radius_count(h, q, r, kernel, offsets, want_total=True, stream=None):
+    tot = ctypes.c_int64(0)
+    _check(load().cg_radius_count(h, _ptr(q), q.shape[0], float(r), kernel, _ptr(offsets),
+                                  ctypes.byref(tot) if want_total else None, _stream(stream)))
+    return tot.value if want_total else None
+
+
+def cg_radius_fill(h, q, r, kernel, offsets, indices, stream=None):
+    _check(load().cg_radius_fill(h, _ptr(q), q.shape[0], float(r), kernel, _ptr(offsets),
+                                 _ptr(indices), _stream(stream)))
+
+
+def cg_all_points_count(h, r, kernel, offsets, want_total=True, stream=None):
+    tot = ctypes.c_int64(0)
+    _check(load().cg_all_points_count(h, float(r), kernel, _ptr(offsets),
+                                      ctypes.byref(tot) if want_total else None, _stream(stream)))
+    return tot.value if want_total else None
+
+
+def cg_all_points_fill(h, r, kernel, offsets, indices, stream=None):
+    _check(load().cg_all_points_fill(h, float(r), kernel, _ptr(offsets), _ptr(indices),
+                                     _stream(stream)))
+
+
+def cg_knn(h, q, k, idx, d2=None, stream=None):
+    _check(load().cg_knn(h, _ptr(q), q.shape[0], int(k), _ptr(idx), _ptr(d2), _stream(stream)))
+
+
+def cg_all_points_knn(h, k, idx, d2=None, stream=None):
+    _check(load().cg_all_points_knn(h, int(k), _ptr(idx), _ptr(d2), _stream(stream)))
+
+
+# ------------------------------------------------------------- convenience
+
+
+class Index:
+    """A device-resident grid index (owns the library handle)."""
+
+    def __init__(self, xyz: torch.Tensor, cell_xy: float, cell_z: float | None = None, dim: int = 2,
+                 flavor: int = DENSE, precision: int = FP32_OFFSET, stream=None):
+        self.n = xyz.shape[0]
+        self.h = cg_build(xyz, cell_xy, cell_z, dim, flavor, precision, stream)
+        self.device = xyz.device
+
+    @classmethod
+    def batched(cls, xyz, tile_offsets, cells, dim=2, flavor=DENSE, precision=FP32_OFFSET, stream=None):
+        self = cls.__new__(cls)
+        self.n = xyz.shape[0]
+        self.h = cg_build_batched(xyz, tile_offsets, cells, dim, flavor, precision, stream)
+        self.device = xyz.device
+        return self
+
+    def info(self) -> dict:
+        return cg_index_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cg_index_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def radius_search(self, q: torch.Tensor | None, r: float, kernel: int = SPHERE, stream=None,
+                      check: bool = True):
+        """CSR (offsets int64 [nq+1], indices int32 [total]); q=None: every point."""
+        nq = self.n if q is None else q.shape[0]
+        offsets = torch.empty(nq + 1, dtype=torch.int64, device=self.device)
+        if q is None:
+            total = cg_all_points_count(self.h, r, kernel, offsets, stream=stream)
+        else:
+            q = _points(q)
+            total = cg_radius_count(self.h, q, r, kernel, offsets, stream=stream)
+        indices = torch.empty(max(total, 1), dtype=torch.int32, device=self.device)
+        if q is None:
+            cg_all_points_fill(self.h, r, kernel, offsets, indices, stream=stream)
+        else:
+            cg_radius_fill(self.h, q, r, kernel, offsets, indices, stream=stream)
+        if check:
+            cg_index_status(self.h, stream)
+        return offsets, indices[:total]
+
+    def knn(self, q: torch.Tensor | None, k: int, with_d2: bool = True, stream=None,
+            check: bool = True):
+        nq = self.n if q is None else q.shape[0]
+        idx = torch.empty((nq, k), dtype=torch.int32, device=self.device)
+        d2 = torch.empty((nq, k), dtype=torch.float64, device=self.device) if with_d2 else None
+        if q is None:
+            cg_all_points_knn(self.h, k, idx, d2, stream=stream)
+        else:
+            cg_knn(self.h, _points(q), k, idx, d2, stream=stream)
+        if check:
+            cg_index_status(self.h, stream)
+        return idx, d2

@@ -1,0 +1,244 @@
+// cg_capi.cu -- the C ABI declared in include/cheesegpu.h: argument checks,
+// error reporting, allocation hooks and the calls into the build / query
+// implementations.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "cg_index.h"
+#include "cg_query.cuh"
+
+namespace cg {
+
+cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, int ntiles,
+                      const double* cell_xy, const double* cell_z, int dim, int flavor,
+                      int precision, cudaStream_t st, cg_index** out);
+cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, double r,
+                      int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
+                      cudaStream_t st);
+cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
+                   double* d2, cudaStream_t st);
+
+namespace {
+thread_local std::string g_last_error;
+cg_alloc_fn g_alloc = nullptr;
+cg_free_fn g_free = nullptr;
+void* g_user = nullptr;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+cg_status fail(cg_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+cg_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  if (g_alloc) return g_alloc(bytes, (void*)st, g_user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+  if (!p) return;
+  if (g_free) {
+    g_free(p, (void*)st, g_user);
+    return;
+  }
+  cudaFreeAsync(p, st);
+}
+
+cg_status check_status(cg_index* ix, cudaStream_t st) {
+  uint32_t w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, ix->status, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status readback");
+  if (w & (ST_NONFINITE | ST_TIMEOUT | ST_OVERFLOW | ST_INTERNAL)) {
+    cudaMemsetAsync(ix->status, 0, 4, st);
+    if (w & ST_NONFINITE) return fail(CG_ERR_INVALID, "non-finite query coordinate");
+    if (w & ST_TIMEOUT) return fail(CG_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (w & ST_OVERFLOW) return fail(CG_ERR_OVERFLOW, "an internal capacity was exceeded");
+    return fail(CG_ERR_INTERNAL, "device consistency check failed");
+  }
+  return CG_OK;
+}
+
+}  // namespace cg
+
+using namespace cg;
+
+static bool finite_pos(double v) { return isfinite(v) && v > 0; }
+
+extern "C" {
+
+cg_status cg_set_allocator(cg_alloc_fn alloc_fn, cg_free_fn free_fn, void* user) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr))
+    return fail(CG_ERR_INVALID, "allocator hook needs both functions or neither");
+  g_alloc = alloc_fn;
+  g_free = free_fn;
+  g_user = user;
+  return CG_OK;
+}
+
+const char* cg_last_error(void) { return g_last_error.c_str(); }
+
+const char* cg_version(void) { return "cheesegpu 0.1 (sm_103a)"; }
+
+cg_status cg_build(const double* xyz_dev, int64_t n, double cell_xy, double cell_z, int dim,
+                   cg_flavor flavor, cg_precision precision, void* stream, cg_index_t* out) {
+  if (!out) return fail(CG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!xyz_dev) return fail(CG_ERR_INVALID, "xyz_dev is NULL");
+  if (n < 1 || n >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "n must be in [1, 2^31)");
+  if (!finite_pos(cell_xy) || !finite_pos(cell_z)) return fail(CG_ERR_INVALID, "cell sizes must be positive and finite");
+  if (dim != 2 && dim != 3) return fail(CG_ERR_INVALID, "dim must be 2 or 3");
+  if (flavor < CG_DENSE || flavor > CG_MIXED) return fail(CG_ERR_INVALID, "unknown flavor");
+  if (precision != CG_FP64 && precision != CG_FP32_OFFSET) return fail(CG_ERR_INVALID, "unknown precision");
+  int64_t toff[2] = {0, n};
+  return build_index(xyz_dev, n, toff, 1, &cell_xy, &cell_z, dim, flavor, precision,
+                     (cudaStream_t)stream, out);
+}
+
+cg_status cg_build_batched(const double* xyz_dev, const int64_t* tile_offsets, int32_t T,
+                           const double* cell_xy_host, int dim, cg_flavor flavor,
+                           cg_precision precision, void* stream, cg_index_t* out) {
+  if (!out) return fail(CG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!xyz_dev || !tile_offsets || !cell_xy_host) return fail(CG_ERR_INVALID, "NULL argument");
+  if (T < 1) return fail(CG_ERR_INVALID, "T must be >= 1");
+  if (dim != 2 && dim != 3) return fail(CG_ERR_INVALID, "dim must be 2 or 3");
+  if (flavor < CG_DENSE || flavor > CG_MIXED) return fail(CG_ERR_INVALID, "unknown flavor");
+  if (precision != CG_FP64 && precision != CG_FP32_OFFSET) return fail(CG_ERR_INVALID, "unknown precision");
+  if (tile_offsets[0] != 0) return fail(CG_ERR_INVALID, "tile_offsets[0] must be 0");
+  for (int t = 0; t < T; ++t) {
+    if (tile_offsets[t + 1] <= tile_offsets[t]) return fail(CG_ERR_INVALID, "every tile must be non-empty");
+    if (!finite_pos(cell_xy_host[t])) return fail(CG_ERR_INVALID, "cell sizes must be positive and finite");
+  }
+  const int64_t n = tile_offsets[T];
+  if (n >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "too many points");
+  return build_index(xyz_dev, n, tile_offsets, T, cell_xy_host, cell_xy_host, dim, flavor,
+                     precision, (cudaStream_t)stream, out);
+}
+
+cg_status cg_index_info(cg_index_t ix, cg_index_info_t* info) {
+  if (!ix || !info) return fail(CG_ERR_INVALID, "NULL argument");
+  memset(info, 0, sizeof *info);
+  info->n = ix->n;
+  info->dim = ix->dim;
+  info->flavor = ix->flavor;
+  info->precision = ix->precision;
+  info->ntiles = ix->ntiles;
+  info->ncell = ix->ncell;
+  info->nonempty = ix->nkeys;
+  info->nslices = ix->nslices;
+  info->dense_slices = ix->dense_slices;
+  info->device_bytes = (int64_t)ix->bufs.bytes;
+  const Tile& T = ix->tiles_host[0];
+  for (int a = 0; a < 3; ++a) {
+    info->lo[a] = T.lo[a];
+    info->hi[a] = T.hi[a];
+    info->nc[a] = T.n[a];
+    info->cell[a] = T.s[a];
+    info->origin[a] = T.origin[a];
+  }
+  info->enc_err = T.enc_err;
+  return CG_OK;
+}
+
+cg_status cg_index_free(cg_index_t ix) {
+  if (!ix) return fail(CG_ERR_INVALID, "NULL index");
+  ix->radius.bufs.release(ix->stream);
+  ix->plan.bufs.release(ix->stream);
+  ix->bufs.release(ix->stream);
+  delete ix;
+  return CG_OK;
+}
+
+cg_status cg_radius_count(cg_index_t ix, const double* q_dev, int64_t nq, double r,
+                          cg_kernel kernel, int64_t* offsets_dev, int64_t* total_host,
+                          void* stream) {
+  if (!ix || !offsets_dev || (nq > 0 && !q_dev)) return fail(CG_ERR_INVALID, "NULL argument");
+  return radius_pass(ix, false, q_dev, nq, r, kernel, false, offsets_dev, nullptr, total_host,
+                     (cudaStream_t)stream);
+}
+
+cg_status cg_radius_fill(cg_index_t ix, const double* q_dev, int64_t nq, double r,
+                         cg_kernel kernel, const int64_t* offsets_dev, int32_t* indices_dev,
+                         void* stream) {
+  if (!ix || !offsets_dev || (nq > 0 && !q_dev)) return fail(CG_ERR_INVALID, "NULL argument");
+  return radius_pass(ix, false, q_dev, nq, r, kernel, true, (int64_t*)offsets_dev, indices_dev,
+                     nullptr, (cudaStream_t)stream);
+}
+
+cg_status cg_all_points_count(cg_index_t ix, double r, cg_kernel kernel, int64_t* offsets_dev,
+                              int64_t* total_host, void* stream) {
+  if (!ix || !offsets_dev) return fail(CG_ERR_INVALID, "NULL argument");
+  return radius_pass(ix, true, nullptr, ix->n, r, kernel, false, offsets_dev, nullptr, total_host,
+                     (cudaStream_t)stream);
+}
+
+cg_status cg_all_points_fill(cg_index_t ix, double r, cg_kernel kernel, const int64_t* offsets_dev,
+                             int32_t* indices_dev, void* stream) {
+  if (!ix || !offsets_dev) return fail(CG_ERR_INVALID, "NULL argument");
+  return radius_pass(ix, true, nullptr, ix->n, r, kernel, true, (int64_t*)offsets_dev, indices_dev,
+                     nullptr, (cudaStream_t)stream);
+}
+
+cg_status cg_radius_search(cg_index_t ix, const double* q_dev, int64_t nq, double r,
+                           cg_kernel kernel, int64_t** offsets_dev, int32_t** indices_dev,
+                           int64_t* total, void* stream) {
+  if (!ix || !offsets_dev || !indices_dev || !total || (nq > 0 && !q_dev))
+    return fail(CG_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  *offsets_dev = nullptr;
+  *indices_dev = nullptr;
+  int64_t* off = (int64_t*)dev_alloc(8 * (size_t)(nq + 1), st);
+  if (!off) return fail(CG_ERR_OOM, "device allocation failed (offsets)");
+  int64_t tot = 0;
+  cg_status s = radius_pass(ix, false, q_dev, nq, r, kernel, false, off, nullptr, &tot, st);
+  if (s != CG_OK) { dev_free(off, st); return s; }
+  int32_t* ind = (int32_t*)dev_alloc(4 * (size_t)std::max<int64_t>(tot, 1), st);
+  if (!ind) { dev_free(off, st); return fail(CG_ERR_OOM, "device allocation failed (indices)"); }
+  s = radius_pass(ix, false, q_dev, nq, r, kernel, true, off, ind, nullptr, st);
+  if (s != CG_OK) { dev_free(off, st); dev_free(ind, st); return s; }
+  *offsets_dev = off;
+  *indices_dev = ind;
+  *total = tot;
+  return CG_OK;
+}
+
+cg_status cg_index_status(cg_index_t ix, void* stream) {
+  if (!ix) return fail(CG_ERR_INVALID, "NULL index");
+  return check_status(ix, (cudaStream_t)stream);
+}
+
+cg_status cg_free_device(void* ptr, void* stream) {
+  dev_free(ptr, (cudaStream_t)stream);
+  return CG_OK;
+}
+
+cg_status cg_knn(cg_index_t ix, const double* q_dev, int64_t nq, int32_t k, int32_t* idx_dev,
+                 double* d2_dev, void* stream) {
+  if (!ix || !idx_dev || (nq > 0 && !q_dev)) return fail(CG_ERR_INVALID, "NULL argument");
+  return knn_pass(ix, false, q_dev, nq, k, idx_dev, d2_dev, (cudaStream_t)stream);
+}
+
+cg_status cg_all_points_knn(cg_index_t ix, int32_t k, int32_t* idx_dev, double* d2_dev,
+                            void* stream) {
+  if (!ix || !idx_dev) return fail(CG_ERR_INVALID, "NULL argument");
+  return knn_pass(ix, true, nullptr, ix->n, k, idx_dev, d2_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// cg_index.h -- host-side index object and device-memory helpers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "cg_internal.cuh"
+
+namespace cg {
+
+// Device allocation through the installed hook, else cudaMallocAsync.
+void* dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+
+// Thread-local last-error message.
+void set_error(const std::string& msg);
+cg_status fail(cg_status s, const std::string& msg);
+cg_status cuda_fail(cudaError_t e, const char* what);
+
+// Scoped list of device buffers owned by an object.
+struct DevBufs {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  void* get(size_t b, cudaStream_t st) {
+    if (b == 0) b = 16;
+    void* p = dev_alloc(b, st);
+    if (p) { ptrs.push_back(p); bytes += b; }
+    return p;
+  }
+  void release(cudaStream_t st) {
+    for (void* p : ptrs) dev_free(p, st);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+struct Thresholds;
+
+// Cached plan of an external query set (query order, blocks, records).
+struct QueryPlan {
+  const double* q = nullptr;
+  int64_t nq = -1;
+  uint64_t version = 0;          // bumps each time a plan is (re)built
+  uint64_t nblocks_host_version = ~0ull;
+  DevBufs bufs;
+  uint32_t nblocks = 0;          // host copy (valid when versions match)
+  uint32_t* nblocks_dev = nullptr;  // [16]: [0] blocks, [4] max |query offset| bits
+  uint32_t* blk_beg = nullptr;   // [nblocks+1] block start in query order
+  uint32_t* blk_key = nullptr;   // [nblocks] voxel key of the block (clamped)
+  float4* qrec = nullptr;        // [nq] sorted: x~, y~, z~, query id bits
+  double4_32a* qrec64 = nullptr;     // [nq] sorted: x, y, z, query id bits (binary64 path)
+};
+
+// State of a radius count pass kept for the matching fill pass.
+struct RadiusState {
+  DevBufs bufs;
+  bool valid = false, all_points = false, stats_known = false;
+  const double* q = nullptr;
+  int64_t nq = 0;
+  double r = 0;
+  int kernel = 0;
+  uint64_t plan_version = 0;
+  uint32_t* counts = nullptr;      // [nq] per query id
+  uint32_t* heavy_list = nullptr;  // rows assembled from several sorted runs
+  uint32_t* heavy_soff = nullptr;  // scratch offsets of long rows
+  uint32_t* ctrs = nullptr;        // [64] counters (see cg_query.cu)
+  Thresholds* thr = nullptr;
+  void* scan_scratch = nullptr;
+  uint32_t heavy_count = 0;
+  uint64_t heavy_scratch = 0;
+  char thr_host[64];
+};
+
+}  // namespace cg
+
+struct cg_index {
+  int dim = 2, flavor = 0, precision = 0, ntiles = 1;
+  int64_t n = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<cg::Tile> tiles_host;
+  cg::DevBufs bufs;
+  cg::Tile* tiles = nullptr;
+  float4* pts32 = nullptr;
+  double4_32a* pts64s = nullptr;
+  double* xyz64 = nullptr;
+  uint32_t* ukeys = nullptr;
+  uint32_t* ustart = nullptr;
+  uint32_t nkeys = 0;
+  uint32_t* cstart = nullptr;
+  unsigned long long* hash = nullptr;
+  uint32_t hash_mask = 0;
+  uint8_t* slice_dense = nullptr;
+  uint32_t* slice_tab_off = nullptr;
+  uint2* mtab = nullptr;
+  int64_t ncell = 0, nslices = 0, dense_slices = 0;
+  uint32_t* status = nullptr;    // device status word (ST_* bits)
+  uint32_t* scratch_u32 = nullptr;  // small device scratch
+  double enc_err0 = 0;
+  cg::QueryPlan plan;
+  cg::RadiusState radius;
+  int max_pts_per_voxel = 0;
+
+  cg::IndexView view() const {
+    cg::IndexView v;
+    v.tiles = tiles;
+    v.ntiles = ntiles;
+    v.dim = dim;
+    v.flavor = flavor;
+    v.precision = precision;
+    v.n = (uint32_t)n;
+    v.nkeys = nkeys;
+    v.pts32 = pts32;
+    v.pts64s = pts64s;
+    v.xyz64 = xyz64;
+    v.ukeys = ukeys;
+    v.ustart = ustart;
+    v.cstart = cstart;
+    v.hash = hash;
+    v.hash_mask = hash_mask;
+    v.slice_dense = slice_dense;
+    v.slice_tab_off = slice_tab_off;
+    v.mtab = mtab;
+    return v;
+  }
+};
+
+namespace cg {
+// Reads and clears the device status word (synchronises the stream).
+cg_status check_status(cg_index* ix, cudaStream_t st);
+}  // namespace cg

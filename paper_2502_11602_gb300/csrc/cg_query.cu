@@ -1,0 +1,862 @@
+// cg_query.cu -- fixed-radius kernel search on the GPU (Algorithm 1 of
+// arXiv 2502.11602, run for a whole batch of queries in two passes).
+//
+// Blocked formulation.  Queries are grouped by the voxel that contains them
+// (for "every point is a query" the groups are the index's own voxel runs).
+// A CTA takes one group: it computes the union of the group's voxel ranges
+// (the bounding box of each kernel mapped through Eq. chs-point-to-idcs,
+// widened by a proven rounding pad), turns every row of that range (2D: one
+// x row; 3D: one (x, y) column) into ONE contiguous span of the sorted points
+// (consecutive global indices, Eqs. indices-to-global), stages the spans'
+// records in shared memory, and tests every query of the group against every
+// staged candidate (the point scan and is_inside of Algorithm 1).
+//
+//   count pass: per-query counts (no order needed)
+//   fill pass : the staged records are first sorted by original id in shared
+//               memory, so each query's hits come out ascending; one warp per
+//               query writes them with a ballot compaction (coalesced rows).
+//
+// Precision.  Binary64 records are tested exactly.  Binary32 offset records
+// are tested in binary32 and a candidate whose binary32 value lies within
+// the proven band [s_lo, s_hi] of r^2 is re-tested with the exact binary64
+// predicate on the original coordinates, so both give the same sets.
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+
+#include <string.h>
+
+#include <algorithm>
+
+#include "cg_query.cuh"
+#include "cg_sort.cuh"
+
+namespace cg {
+
+// ----------------------------------------------------------------- thresholds
+
+namespace {
+__host__ __device__ inline float f_down(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2float_rd(x);
+#else
+  float f = (float)x;
+  if ((double)f > x) f = nextafterf(f, -INFINITY);
+  return f;
+#endif
+}
+__host__ __device__ inline float f_up(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2float_ru(x);
+#else
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+#endif
+}
+}  // namespace
+
+// Binary32 offset test, error model.  Per axis the binary32 difference
+// dxf = fl32(x~_p - x~_c) and the exact dx = fl64(p - c) satisfy
+//   |dxf - dx| <= alpha + beta |dx|,  alpha = (e_p + e_q)(1 + u),
+//   beta = (u + U)(1 + 2U),  u = 2^-24, U = 2^-53,
+// where e_p, e_q bound |x~ - (x - O)| (binary32 rounding of the offset plus
+// the binary64 rounding of x - O).  With S = sum dx^2 and Sf = sum dxf^2:
+//   |Sf - S| <= c1 sqrt(S) + c0 + c2 S,  c1 = 2 alpha (1 + beta) sqrt(3),
+//   c0 = 3 alpha^2, c2 = 2 beta + beta^2 (Cauchy-Schwarz on the three axes).
+// The binary32 value d2f is within 3.0000002 u Sf of Sf (three roundings) and
+// the binary64 value d2 within 3.0000001 U S of S.  Hence
+//   d2f <= T_lo  =>  d2 <= r2     T_lo = (S_in (1 - c2) - c1 sqrt(S_in) - c0)(1 - 3.0000002u)
+//   d2f >  T_hi  =>  d2 >  r2     T_hi = (S_mx (1 + c2) + c1 sqrt(S_mx) + c0)(1 + 3.0000002u)
+// with S_in = r2 (1 - 4U), S_mx = r2 (1 + 4U); the margins are doubled for
+// headroom.  The cube uses the same argument on each axis alone.
+__host__ __device__ Thresholds make_thresholds(double r, double e_p, double e_q) {
+  const double u = 5.9604644775390625e-08;   // 2^-24
+  const double U = 1.1102230246251565e-16;   // 2^-53
+  Thresholds t;
+  t.r2 = r * r;
+  const double r2 = t.r2;
+  const double alpha = (e_p + e_q) * (1.0 + u);
+  const double beta = (u + U) * (1.0 + 2.0 * U);
+  const double c1 = 2.0 * alpha * (1.0 + beta) * 1.7320508075688774;
+  const double c0 = 3.0 * alpha * alpha;
+  const double c2 = 2.0 * beta + beta * beta;
+  const double s_in = r2 * (1.0 - 4.0 * U);
+  const double s_mx = r2 * (1.0 + 4.0 * U);
+  double t_lo = (s_in * (1.0 - c2) - c1 * sqrt(s_in) - c0) * (1.0 - 3.0000002 * u);
+  double t_hi = (s_mx * (1.0 + c2) + c1 * sqrt(s_mx) + c0) * (1.0 + 3.0000002 * u);
+  t_lo = r2 - 2.0 * (r2 - t_lo);
+  t_hi = r2 + 2.0 * (t_hi - r2);
+  t.s_lo = t_lo > 0 ? f_down(t_lo) : -1.0f;
+  t.s_hi = f_up(t_hi);
+  // cube: one axis, |dx| <= r (1 + U) when fl64(dx^2) <= r2
+  const double rin = sqrt(r2 * (1.0 - 2.0 * U)) * (1.0 - beta) - alpha;
+  double c_lo = rin > 0 ? (1.0 - 1.0000001 * u) * rin * rin : -1.0;
+  const double rmx = sqrt(r2 * (1.0 + 2.0 * U)) * (1.0 + beta) + alpha;
+  double c_hi = (1.0 + 1.0000001 * u) * rmx * rmx;
+  c_lo = r2 - 2.0 * (r2 - c_lo);
+  c_hi = r2 + 2.0 * (c_hi - r2);
+  t.c_lo = c_lo > 0 ? f_down(c_lo) : -1.0f;
+  t.c_hi = f_up(c_hi);
+  t.r_f = f_up(r);
+  t.e_q = f_up(e_q);
+  t.pad_[0] = t.pad_[1] = 0.f;
+  return t;
+}
+
+namespace {
+
+constexpr int RT = 256;         // threads per CTA
+constexpr int RW = RT / 32;     // warps per CTA
+constexpr int QB = 128;         // queries per sub-block
+constexpr int MAX_SPANS = 256;  // spans staged per group of rows
+
+template <int PREC> struct RecT;
+template <> struct RecT<1> { using T = float4; static constexpr int KMAX = 4096; };
+template <> struct RecT<0> { using T = double4_32a; static constexpr int KMAX = 2048; };
+
+__device__ __forceinline__ uint32_t rec_id(const float4& r) { return __float_as_uint(r.w); }
+__device__ __forceinline__ uint32_t rec_id(const double4_32a& r) {
+  return (uint32_t)__double_as_longlong(r.w);
+}
+__device__ __forceinline__ float4 rec_sentinel(float4*) {
+  return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+}
+__device__ __forceinline__ double4_32a rec_sentinel(double4_32a*) {
+  return make_double4_32a(0.0, 0.0, 0.0, __longlong_as_double(0xffffffffll));
+}
+
+// exact predicate on the original binary64 coordinates (no contraction)
+template <int KERN>
+__device__ __forceinline__ bool exact_inside(const double* __restrict__ p,
+                                             const double* __restrict__ c, double r2) {
+  double dx = __dsub_rn(__ldg(p), __ldg(c));
+  double dy = __dsub_rn(__ldg(p + 1), __ldg(c + 1));
+  double dz = __dsub_rn(__ldg(p + 2), __ldg(c + 2));
+  if (KERN == CG_SPHERE) {
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 <= r2;
+  }
+  double m = fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return m <= r2;
+}
+
+template <int KERN>
+__device__ __forceinline__ bool exact_inside4(const double4_32a& p, const double4_32a& c, double r2) {
+  double dx = __dsub_rn(p.x, c.x);
+  double dy = __dsub_rn(p.y, c.y);
+  double dz = __dsub_rn(p.z, c.z);
+  if (KERN == CG_SPHERE) {
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 <= r2;
+  }
+  double m = fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return m <= r2;
+}
+
+// binary32 screen; returns 1 inside, 0 outside, 2 undecided
+template <int KERN>
+__device__ __forceinline__ int screen32(const float4& c, const float4& q, const Thresholds& t) {
+  float dx = __fsub_rn(c.x, q.x);
+  float dy = __fsub_rn(c.y, q.y);
+  float dz = __fsub_rn(c.z, q.z);
+  float v;
+  float lo, hi;
+  if (KERN == CG_SPHERE) {
+    v = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    lo = t.s_lo; hi = t.s_hi;
+  } else {
+    v = fmaxf(fmaxf(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    lo = t.c_lo; hi = t.c_hi;
+  }
+  if (v <= lo) return 1;
+  if (v <= hi) return 2;
+  return 0;
+}
+
+template <class R>
+__device__ void bitonic_sort_by_id(R* a, int P) {
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        int lo = 2 * j * (i / j) + (i % j);
+        int hi = lo + j;
+        bool asc = (lo & k) == 0;
+        R x = a[lo], y = a[hi];
+        if ((rec_id(x) > rec_id(y)) == asc) { a[lo] = y; a[hi] = x; }
+      }
+      __syncthreads();
+    }
+}
+
+// Voxel coordinate u = (x - p-) / s of a query record, in binary32.
+__device__ __forceinline__ float rec_u(const float4& q, const Tile& T, int a) {
+  float x = a == 0 ? q.x : (a == 1 ? q.y : q.z);
+  return __fmul_rn(__fadd_rn(x, T.D[a]), T.inv_sf[a]);
+}
+__device__ __forceinline__ float rec_u(const double4_32a& q, const Tile& T, int a) {
+  double x = a == 0 ? q.x : (a == 1 ? q.y : q.z);
+  return __fmul_rn(__double2float_rn(__dsub_rn(x, T.lo[a])), T.inv_sf[a]);
+}
+__device__ __forceinline__ float rec_abs_off(const float4& q, int a) {
+  return fabsf(a == 0 ? q.x : (a == 1 ? q.y : q.z));
+}
+__device__ __forceinline__ float rec_abs_off(const double4_32a&, int) { return 0.f; }
+
+struct HeavyOut {
+  uint32_t* list;        // [cap] (query id, or id | 0x80000000 for rows needing scratch)
+  uint32_t* count;       // number of entries
+  unsigned long long* scratch_total;  // total scratch elements for long rows
+  uint32_t* scratch_off; // [cap] scratch offset of each entry
+  uint32_t* max_len;
+  uint32_t cap;
+};
+
+constexpr uint32_t kSmemSortCap = 8192;  // rows up to this length sort in shared memory
+
+template <int PREC, int KERN, bool FILL>
+__global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
+                                                    const Thresholds* __restrict__ thr_p,
+                                                    uint32_t* __restrict__ counts,
+                                                    const int64_t* __restrict__ offsets,
+                                                    int32_t* __restrict__ out, HeavyOut heavy,
+                                                    unsigned* work_ctr, uint32_t* status) {
+  using R = typename RecT<PREC>::T;
+  constexpr int KMAX = RecT<PREC>::KMAX;
+  extern __shared__ __align__(32) unsigned char smem[];
+  R* rec = reinterpret_cast<R*>(smem);
+  R* qr = rec + KMAX;
+  long long* q_pos = reinterpret_cast<long long*>(qr + QB);
+  uint32_t* q_cnt = reinterpret_cast<uint32_t*>(q_pos + QB);
+  uint32_t* s_start = q_cnt + QB;
+  uint32_t* s_off = s_start + MAX_SPANS;  // [MAX_SPANS + 1]
+  __shared__ int s_lo[3], s_hi[3];
+  __shared__ uint32_t s_blk;
+
+  const Thresholds thr = *thr_p;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32)
+                                        : reinterpret_cast<const R*>(ix.pts64s);
+  const R* __restrict__ qsrc = qs.all_points ? pts
+                                             : (PREC == 1 ? reinterpret_cast<const R*>(qs.qrec)
+                                                          : reinterpret_cast<const R*>(qs.qrec64));
+  const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_blk = atomicAdd(work_ctr, 1u);
+    __syncthreads();
+    const uint32_t b = s_blk;
+    if (b >= qs.nblocks) break;
+    const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
+    const uint32_t bkey = qs.blk_key[b];
+    const int ti = ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey);
+    const Tile& T = ix.tiles[ti];
+    const int dim = ix.dim;
+
+    for (uint32_t q0 = qb0; q0 < qb1; q0 += QB) {
+      const int nqb = (int)min((uint32_t)QB, qb1 - q0);
+      if (threadIdx.x < 3) { s_lo[threadIdx.x] = INT_MAX; s_hi[threadIdx.x] = INT_MIN; }
+      __syncthreads();
+      // queries of the sub-block and the union of their voxel ranges
+      {
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        for (int t = threadIdx.x; t < nqb; t += RT) {
+          R q = qsrc[q0 + t];
+          qr[t] = q;
+          q_cnt[t] = 0;
+          if (FILL) q_pos[t] = offsets[rec_id(q)];
+          for (int a = 0; a < dim; ++a) {
+            float u = rec_u(q, T, a);
+            float rr = __fmul_ru(__fmul_ru(thr.r_f, T.inv_sf[a]), 1.0000005f);
+            float pad = __fadd_ru(__fadd_ru(rr, T.eta),
+                                  __fmul_ru(__fadd_ru(fabsf(u), rec_abs_off(q, a) * T.inv_sf[a]), 3.0e-7f));
+            pad = __fadd_ru(pad, __fmul_ru(thr.e_q, T.inv_sf[a]));
+            float ul = fminf(fmaxf(__fsub_rd(u, pad), -1.0e9f), 1.0e9f);
+            float uh = fminf(fmaxf(__fadd_ru(u, pad), -1.0e9f), 1.0e9f);
+            lo[a] = min(lo[a], (int)floorf(ul));
+            hi[a] = max(hi[a], (int)floorf(uh));
+          }
+        }
+        for (int a = 0; a < dim; ++a) {
+          for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+          }
+          if (lane == 0) { atomicMin(&s_lo[a], lo[a]); atomicMax(&s_hi[a], hi[a]); }
+        }
+      }
+      __syncthreads();
+      int lo[3], hi[3];
+      bool empty = false;
+      for (int a = 0; a < 3; ++a) {
+        if (a < dim) {
+          lo[a] = max(s_lo[a], 0);
+          hi[a] = min(s_hi[a], T.n[a] - 1);
+          empty |= lo[a] > hi[a];
+        } else {
+          lo[a] = 0;
+          hi[a] = T.n[a] - 1;
+        }
+      }
+      int nchunks = 0;
+      if (!empty) {
+        const int ni = hi[0] - lo[0] + 1, nj = hi[1] - lo[1] + 1;
+        const int nsp_total = dim == 2 ? ni : ni * nj;
+        for (int sg = 0; sg < nsp_total; sg += MAX_SPANS) {
+          const int nsp = min(MAX_SPANS, nsp_total - sg);
+          for (int s = threadIdx.x; s < nsp; s += RT) {
+            int id = sg + s;
+            uint32_t k0, k1;
+            if (dim == 2) {
+              uint32_t row = (uint32_t)(lo[0] + id) * (uint32_t)T.n[1];
+              k0 = T.key_base + row + (uint32_t)lo[1];
+              k1 = T.key_base + row + (uint32_t)hi[1];
+            } else {
+              int i = lo[0] + id / nj, j = lo[1] + id % nj;
+              uint32_t col = ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) * (uint32_t)T.n[2];
+              k0 = T.key_base + col + (uint32_t)lo[2];
+              k1 = T.key_base + col + (uint32_t)hi[2];
+            }
+            uint2 sp = row_span(ix, T, k0, k1);
+            s_start[s] = sp.x;
+            s_off[s] = sp.y - sp.x;
+          }
+          __syncthreads();
+          if (warp == 0) {  // exclusive scan of the span lengths (nsp <= 256)
+            uint32_t v[MAX_SPANS / 32];
+            uint32_t run = 0;
+#pragma unroll
+            for (int k = 0; k < MAX_SPANS / 32; ++k) {
+              int s = lane * (MAX_SPANS / 32) + k;
+              uint32_t x = s < nsp ? s_off[s] : 0u;
+              v[k] = run;
+              run += x;
+            }
+            uint32_t incl = run;
+            for (int o = 1; o < 32; o <<= 1) {
+              uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= (unsigned)o) incl += y;
+            }
+            uint32_t base = incl - run;
+#pragma unroll
+            for (int k = 0; k < MAX_SPANS / 32; ++k) {
+              int s = lane * (MAX_SPANS / 32) + k;
+              if (s < nsp) s_off[s] = base + v[k];
+            }
+            if (lane == 31) s_off[nsp] = incl;
+          }
+          __syncthreads();
+          const uint32_t ktot = s_off[nsp];
+          for (uint32_t c0 = 0; c0 < ktot; c0 += KMAX) {
+            const int K = (int)min((uint32_t)KMAX, ktot - c0);
+            for (int t = threadIdx.x; t < K; t += RT) {
+              uint32_t g = c0 + (uint32_t)t;
+              int a = 0, bb = nsp - 1;  // last span with s_off <= g
+              while (a < bb) {
+                int m = (a + bb + 1) >> 1;
+                if (s_off[m] <= g) a = m; else bb = m - 1;
+              }
+              rec[t] = pts[s_start[a] + (g - s_off[a])];
+            }
+            if (FILL) {
+              int P = 32;
+              while (P < K) P <<= 1;
+              for (int t = K + threadIdx.x; t < P; t += RT) rec[t] = rec_sentinel((R*)nullptr);
+              __syncthreads();
+              bitonic_sort_by_id(rec, P);
+            } else {
+              __syncthreads();
+            }
+            // test: one warp per query, one lane per candidate
+            for (int qi = warp; qi < nqb; qi += RW) {
+              const R q = qr[qi];
+              const uint32_t qid = rec_id(q);
+              uint32_t cnt = 0;
+              long long pos = FILL ? q_pos[qi] : 0;
+              const long long lim = FILL ? offsets[qid + 1] : 0;
+              for (int j0 = 0; j0 < K; j0 += 32) {
+                const int j = j0 + (int)lane;
+                bool in = false;
+                uint32_t cid = 0;
+                if (j < K) {
+                  const R c = rec[j];
+                  cid = rec_id(c);
+                  if constexpr (PREC == 1) {
+                    int sres = screen32<KERN>(c, q, thr);
+                    in = sres == 1;
+                    if (sres == 2) in = exact_inside<KERN>(ix.xyz64 + 3 * (size_t)cid, q64 + 3 * (size_t)qid, thr.r2);
+                  } else {
+                    in = exact_inside4<KERN>(c, q, thr.r2);
+                  }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (FILL) {
+                  if (in) {
+                    const long long w = pos + __popc(m & lanemask_lt());
+                    if (w < lim) out[w] = (int32_t)cid;   // never past the row
+                    else atomicOr(status, ST_INTERNAL);
+                  }
+                  pos += __popc(m);
+                } else {
+                  cnt += __popc(m);
+                }
+              }
+              if (lane == 0) {
+                if (FILL) q_pos[qi] = pos; else q_cnt[qi] += cnt;
+              }
+            }
+            __syncthreads();
+            ++nchunks;
+          }
+        }
+      }
+      // results of the sub-block
+      for (int t = threadIdx.x; t < nqb; t += RT) {
+        const uint32_t qid = rec_id(qr[t]);
+        if (!FILL) {
+          const uint32_t c = q_cnt[t];
+          counts[qid] = c;
+          if (nchunks > 1 && c > 1) {  // rows made of several sorted runs
+            uint32_t slot = atomicAdd(heavy.count, 1u);
+            if (slot < heavy.cap) {
+              uint32_t tag = 0, soff = 0;
+              if (c > kSmemSortCap) {
+                tag = 0x80000000u;
+                soff = (uint32_t)atomicAdd(heavy.scratch_total, (unsigned long long)c);
+              }
+              heavy.list[slot] = qid | tag;
+              heavy.scratch_off[slot] = soff;
+              atomicMax(heavy.max_len, c);
+            } else {
+              atomicOr(status, ST_OVERFLOW);
+            }
+          }
+        } else if (q_pos[t] != offsets[qid + 1]) {
+          atomicOr(status, ST_INTERNAL);  // fill disagrees with the count pass
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------------------- row sort
+
+// Sorts the rows listed by the count pass (rows assembled from several
+// sorted runs).  Short rows: bitonic sort in shared memory.  Long rows:
+// shared-memory sorted tiles, then pairwise merges through a scratch buffer
+// (merge path), ping-ponging until one run remains.
+__global__ void __launch_bounds__(512) row_sort_kernel(const uint32_t* __restrict__ list,
+                                                       const uint32_t* __restrict__ scratch_off,
+                                                       const uint32_t* __restrict__ count_p,
+                                                       uint32_t cap, const int64_t* __restrict__ off,
+                                                       int32_t* __restrict__ out,
+                                                       int32_t* __restrict__ scratch) {
+  extern __shared__ int32_t sbuf[];  // kSmemSortCap entries
+  uint32_t cnt = min(*count_p, cap);
+  for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+    const uint32_t ent = list[e];
+    const uint32_t qid = ent & 0x7fffffffu;
+    int32_t* row = out + off[qid];
+    const int64_t L = off[qid + 1] - off[qid];
+    // sort tiles of kSmemSortCap in shared memory
+    for (int64_t t0 = 0; t0 < L; t0 += kSmemSortCap) {
+      const int n = (int)(L - t0 < (int64_t)kSmemSortCap ? L - t0 : (int64_t)kSmemSortCap);
+      int P = 1;
+      while (P < n) P <<= 1;
+      for (int i = threadIdx.x; i < P; i += blockDim.x) sbuf[i] = i < n ? row[t0 + i] : INT_MAX;
+      __syncthreads();
+      for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+            int lo = 2 * j * (i / j) + (i % j), hi = lo + j;
+            bool asc = (lo & k) == 0;
+            int32_t x = sbuf[lo], y = sbuf[hi];
+            if ((x > y) == asc) { sbuf[lo] = y; sbuf[hi] = x; }
+          }
+          __syncthreads();
+        }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) row[t0 + i] = sbuf[i];
+      __syncthreads();
+    }
+    if (L <= (int64_t)kSmemSortCap) continue;
+    // merge passes
+    int32_t* src = row;
+    int32_t* dst = scratch + scratch_off[e];
+    for (int64_t w = kSmemSortCap; w < L; w <<= 1) {
+      for (int64_t a0 = 0; a0 < L; a0 += 2 * w) {
+        const int64_t a1 = min(a0 + w, L), b1 = min(a0 + 2 * w, L);
+        const int64_t na = a1 - a0, nb = b1 - a1, tot = na + nb;
+        const int64_t per = (tot + blockDim.x - 1) / blockDim.x;
+        const int64_t d0 = min((int64_t)threadIdx.x * per, tot);
+        const int64_t d1 = min(d0 + per, tot);
+        // merge path: split of diagonal d0
+        int64_t lo = max((int64_t)0, d0 - nb), hi = min(d0, na);
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (src[a0 + mid] <= src[a1 + d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+        }
+        int64_t ia = lo, ib = d0 - lo;
+        for (int64_t d = d0; d < d1; ++d) {
+          bool take_a = ib >= nb || (ia < na && src[a0 + ia] <= src[a1 + ib]);
+          dst[a0 + d] = take_a ? src[a0 + ia++] : src[a1 + ib++];
+        }
+      }
+      __syncthreads();
+      int32_t* t = src; src = dst; dst = t;
+    }
+    if (src != row)
+      for (int64_t i = threadIdx.x; i < L; i += blockDim.x) row[i] = src[i];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------- external queries
+
+__global__ void query_key_kernel(const double* __restrict__ q, int64_t nq, const Tile* __restrict__ tiles,
+                                 int dim, uint32_t* __restrict__ keys, uint32_t* maxoff_bits,
+                                 uint32_t* status) {
+  const Tile& T = tiles[0];
+  float mx = 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nq;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int c[3] = {0, 0, 0};
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) {
+      double x = q[3 * p + a];
+      if (!isfinite(x)) { bad = true; continue; }
+      mx = fmaxf(mx, fabsf(__double2float_ru(__dsub_rn(x, T.origin[a]))));
+      if (a < dim) {
+        double d = __dsub_rn(x, T.lo[a]);
+        double v = floor(__ddiv_rn(d, T.s[a]));
+        v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
+        c[a] = (int)v;
+      }
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    uint32_t g = dim == 2 ? (uint32_t)c[0] * (uint32_t)T.n[1] + (uint32_t)c[1]
+                          : ((uint32_t)c[0] * (uint32_t)T.n[1] + (uint32_t)c[1]) * (uint32_t)T.n[2] + (uint32_t)c[2];
+    keys[p] = T.key_base + g;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxoff_bits, __float_as_uint(mx));
+}
+
+__global__ void query_gather_kernel(const double* __restrict__ q, int64_t nq,
+                                    const uint32_t* __restrict__ perm, const Tile* __restrict__ tiles,
+                                    float4* __restrict__ qrec, double4_32a* __restrict__ qrec64) {
+  const Tile& T = tiles[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t id = perm[i];
+    double x = q[3 * (size_t)id], y = q[3 * (size_t)id + 1], z = q[3 * (size_t)id + 2];
+    if (qrec)
+      qrec[i] = make_float4(__double2float_rn(__dsub_rn(x, T.origin[0])),
+                            __double2float_rn(__dsub_rn(y, T.origin[1])),
+                            __double2float_rn(__dsub_rn(z, T.origin[2])), __uint_as_float(id));
+    if (qrec64) qrec64[i] = make_double4_32a(x, y, z, __longlong_as_double((long long)id));
+  }
+}
+
+__global__ void qrun_flag_kernel(const uint32_t* __restrict__ skeys, int64_t n, uint32_t* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || skeys[i] != skeys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void qrun_emit_kernel(const uint32_t* __restrict__ skeys, int64_t n,
+                                 const uint32_t* __restrict__ flag, const uint32_t* __restrict__ rank,
+                                 uint32_t* __restrict__ bkey, uint32_t* __restrict__ bbeg,
+                                 uint32_t* nblocks) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[i]) { bkey[rank[i]] = skeys[i]; bbeg[rank[i]] = (uint32_t)i; }
+    if (i == n - 1) { bbeg[rank[n]] = (uint32_t)n; *nblocks = rank[n]; }
+  }
+}
+
+__global__ void thresholds_kernel(Thresholds* out, double r, double e_p, const uint32_t* maxoff_bits) {
+  // the query encode bound from the largest query offset magnitude
+  double m = (double)__uint_as_float(*maxoff_bits);
+  double e_q = ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30;
+  *out = make_thresholds(r, e_p, e_q);
+}
+
+int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+template <int PREC>
+size_t radius_smem() {
+  using R = typename RecT<PREC>::T;
+  return sizeof(R) * (RecT<PREC>::KMAX + QB) + sizeof(long long) * QB + 4 * QB + 4 * (2 * MAX_SPANS + 1);
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- host side
+
+cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st) {
+  QueryPlan& P = ix->plan;
+  if (P.q == q && P.nq == nq && P.nblocks_dev) return CG_OK;
+  P.bufs.release(st);
+  P.q = q;
+  P.nq = nq;
+  P.version++;
+  DevBufs tmp;
+  auto bail = [&](cg_status s, const std::string& m) {
+    tmp.release(st);
+    P.bufs.release(st);
+    P.q = nullptr;
+    P.nq = -1;
+    P.nblocks_dev = nullptr;
+    return fail(s, m);
+  };
+  const int64_t n = std::max<int64_t>(nq, 1);
+  uint32_t *keys = (uint32_t*)tmp.get(4 * n, st), *skeys = (uint32_t*)tmp.get(4 * n, st),
+           *perm = (uint32_t*)tmp.get(4 * n, st), *flag = (uint32_t*)tmp.get(4 * n, st),
+           *rank = (uint32_t*)tmp.get(4 * (n + 1), st);
+  void* sort_scratch = tmp.get(radix_sort_scratch_bytes(n), st);
+  void* scan_scratch = tmp.get(scan_scratch_bytes(n), st);
+  P.blk_beg = (uint32_t*)P.bufs.get(4 * (n + 1), st);
+  P.blk_key = (uint32_t*)P.bufs.get(4 * n, st);
+  P.nblocks_dev = (uint32_t*)P.bufs.get(64, st);
+  if (ix->precision == CG_FP32_OFFSET) P.qrec = (float4*)P.bufs.get(16 * n, st);
+  else P.qrec64 = (double4_32a*)P.bufs.get(32 * n, st);
+  if (!keys || !skeys || !perm || !flag || !rank || !sort_scratch || !scan_scratch || !P.blk_beg ||
+      !P.blk_key || !P.nblocks_dev || (!P.qrec && !P.qrec64))
+    return bail(CG_ERR_OOM, "device allocation failed (query plan)");
+  cudaError_t e = cudaMemsetAsync(P.nblocks_dev, 0, 64, st);
+  if (nq > 0) {
+    query_key_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, ix->tiles, ix->dim, keys,
+                                                         P.nblocks_dev + 4, ix->status);
+    const Tile& T = ix->tiles_host[0];
+    int bits = 0;
+    uint64_t kmax = (uint64_t)T.key_base + (uint64_t)T.n[0] * T.n[1] * T.n[2];
+    while (bits < 32 && ((uint64_t)1 << bits) < kmax) ++bits;
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, nq, bits, skeys, perm, sort_scratch, ix->status, st);
+    query_gather_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, perm, ix->tiles, P.qrec, P.qrec64);
+    qrun_flag_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag);
+    if (e == cudaSuccess) e = exclusive_scan_u32_u32(flag, rank, nq, scan_scratch, ix->status, st);
+    qrun_emit_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag, rank, P.blk_key, P.blk_beg,
+                                                        P.nblocks_dev);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  tmp.release(st);
+  if (e != cudaSuccess) return bail(CG_ERR_CUDA, std::string("query plan: ") + cudaGetErrorString(e));
+  return CG_OK;
+}
+
+namespace {
+
+struct RadiusLaunch {
+  IndexView iv;
+  QuerySet qs;
+  const Thresholds* thr;
+};
+
+template <int PREC, int KERN, bool FILL>
+cudaError_t launch_radius(const RadiusLaunch& L, uint32_t* counts, const int64_t* offsets, int32_t* out,
+                          const HeavyOut& heavy, unsigned* work_ctr, uint32_t* status, int grid,
+                          cudaStream_t st) {
+  auto kern = radius_kernel<PREC, KERN, FILL>;
+  const size_t smem = radius_smem<PREC>();
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  kern<<<grid, RT, smem, st>>>(L.iv, L.qs, L.thr, counts, offsets, out, heavy, work_ctr, status);
+  return cudaGetLastError();
+}
+
+template <bool FILL>
+cudaError_t dispatch_radius(int prec, int kern, const RadiusLaunch& L, uint32_t* counts,
+                            const int64_t* offsets, int32_t* out, const HeavyOut& heavy,
+                            unsigned* work_ctr, uint32_t* status, int grid, cudaStream_t st) {
+  if (prec == CG_FP32_OFFSET) {
+    if (kern == CG_SPHERE)
+      return launch_radius<1, CG_SPHERE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+    return launch_radius<1, CG_CUBE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+  }
+  if (kern == CG_SPHERE)
+    return launch_radius<0, CG_SPHERE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+  return launch_radius<0, CG_CUBE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+}
+
+int radius_grid(int prec) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  size_t smem = prec == CG_FP32_OFFSET ? radius_smem<1>() : radius_smem<0>();
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
+  return sms * per_sm;
+}
+
+}  // namespace
+
+// Radius pass state kept on the index between the count and fill calls.
+cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, double r, int kernel,
+                      bool fill, int64_t* offsets, int32_t* out, int64_t* total_host, cudaStream_t st) {
+  if (!(r > 0) || !isfinite(r)) return fail(CG_ERR_INVALID, "radius must be positive and finite");
+  if (kernel != CG_SPHERE && kernel != CG_CUBE) return fail(CG_ERR_INVALID, "unknown kernel");
+  if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
+  if (!all_points && ix->ntiles != 1)
+    return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
+  RadiusState& R = ix->radius;
+  if (!all_points) {
+    cg_status s = prepare_queries(ix, q, nq, st);
+    if (s != CG_OK) return s;
+  }
+  // per-call device state (counts, heavy list, thresholds, counters)
+  const int64_t nqq = all_points ? ix->n : nq;
+  if (!fill) {
+    R.bufs.release(st);
+    R.valid = false;
+    R.counts = (uint32_t*)R.bufs.get(4 * std::max<int64_t>(nqq, 1), st);
+    R.heavy_list = (uint32_t*)R.bufs.get(4 * std::max<int64_t>(nqq, 1), st);
+    R.heavy_soff = (uint32_t*)R.bufs.get(4 * std::max<int64_t>(nqq, 1), st);
+    R.ctrs = (uint32_t*)R.bufs.get(256, st);
+    R.thr = (Thresholds*)R.bufs.get(sizeof(Thresholds), st);
+    R.scan_scratch = R.bufs.get(scan_scratch_bytes(std::max<int64_t>(nqq, 1)), st);
+    if (!R.counts || !R.heavy_list || !R.heavy_soff || !R.ctrs || !R.thr || !R.scan_scratch)
+      return fail(CG_ERR_OOM, "device allocation failed (radius pass)");
+    R.all_points = all_points;
+    R.q = q;
+    R.nq = nqq;
+    R.r = r;
+    R.kernel = kernel;
+    R.plan_version = ix->plan.version;
+    cudaError_t e = cudaMemsetAsync(R.ctrs, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    double emax = 0;
+    for (const Tile& T : ix->tiles_host) emax = std::max(emax, (double)T.enc_err);
+    if (all_points) {
+      Thresholds th = make_thresholds(r, emax, emax);
+      e = cudaMemcpyAsync(R.thr, &th, sizeof th, cudaMemcpyHostToDevice, st);
+      static_assert(sizeof(th) <= sizeof(R.thr_host), "threshold copy");
+      memcpy(R.thr_host, &th, sizeof th);
+    } else {
+      thresholds_kernel<<<1, 1, 0, st>>>(R.thr, r, emax, ix->plan.nblocks_dev + 4);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "thresholds");
+  } else {
+    if (!R.counts || R.all_points != all_points || R.q != q || R.nq != nqq || R.r != r ||
+        R.kernel != kernel || R.plan_version != ix->plan.version)
+      return fail(CG_ERR_INVALID, "radius fill without a matching count pass");
+  }
+  RadiusLaunch L;
+  L.iv = ix->view();
+  L.thr = R.thr;
+  if (all_points) {
+    L.qs.all_points = 1;
+    L.qs.nq = (uint32_t)ix->n;
+    L.qs.nblocks = ix->nkeys;
+    L.qs.blk_beg = ix->ustart;
+    L.qs.blk_key = ix->ukeys;
+    L.qs.qrec = ix->pts32;
+    L.qs.qrec64 = ix->pts64s;
+    L.qs.q64 = ix->xyz64;
+  } else {
+    QueryPlan& P = ix->plan;
+    L.qs.all_points = 0;
+    L.qs.nq = (uint32_t)nq;
+    L.qs.nblocks = 0xffffffffu;  // read from the device below
+    L.qs.blk_beg = P.blk_beg;
+    L.qs.blk_key = P.blk_key;
+    L.qs.qrec = P.qrec;
+    L.qs.qrec64 = P.qrec64;
+    L.qs.q64 = q;
+  }
+  HeavyOut H;
+  H.list = R.heavy_list;
+  H.scratch_off = R.heavy_soff;
+  H.count = R.ctrs + 0;
+  H.max_len = R.ctrs + 1;
+  H.scratch_total = (unsigned long long*)(R.ctrs + 2);
+  H.cap = (uint32_t)std::max<int64_t>(nqq, 1);
+  unsigned* work = R.ctrs + (fill ? 8 : 6);
+  cudaError_t e = cudaSuccess;
+  if (fill) {
+    e = cudaMemsetAsync(work, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+  }
+  if (!all_points) {
+    // the block count lives on the device: copy it into the launch struct
+    // through a tiny synchronous read only once per plan
+    if (ix->plan.nblocks_host_version != ix->plan.version) {
+      e = cudaMemcpyAsync(&ix->plan.nblocks, ix->plan.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "query plan readback");
+      ix->plan.nblocks_host_version = ix->plan.version;
+    }
+    L.qs.nblocks = ix->plan.nblocks;
+  }
+  const int grid = radius_grid(ix->precision);
+  if (nqq > 0 && L.qs.nblocks > 0) {
+    if (!fill) {
+      e = dispatch_radius<false>(ix->precision, kernel, L, R.counts, nullptr, nullptr, H, work, ix->status, grid, st);
+    } else {
+      e = dispatch_radius<true>(ix->precision, kernel, L, nullptr, offsets, out, H, work, ix->status, grid, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "radius kernel");
+  }
+  if (!fill) {
+    if (nqq > 0) {
+      e = exclusive_scan_u32_i64(R.counts, offsets, nqq, R.scan_scratch, ix->status, st);
+    } else {
+      e = cudaMemsetAsync(offsets, 0, 8, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "offsets scan");
+    uint32_t stats[4] = {0, 0, 0, 0};
+    if (total_host) {
+      e = cudaMemcpyAsync(total_host, offsets + nqq, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(stats, R.ctrs, 16, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "count readback");
+      R.heavy_count = stats[0];
+      R.heavy_scratch = ((uint64_t)stats[3] << 32) | stats[2];
+      R.stats_known = true;
+      cg_status s = check_status(ix, st);
+      if (s != CG_OK) return s;
+    } else {
+      R.stats_known = false;
+    }
+    R.valid = true;
+    return CG_OK;
+  }
+  // fill: sort the rows that were assembled from several runs
+  if (!R.stats_known) {
+    uint32_t stats[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(stats, R.ctrs, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy readback");
+    R.heavy_count = stats[0];
+    R.heavy_scratch = ((uint64_t)stats[3] << 32) | stats[2];
+    R.stats_known = true;
+  }
+  if (R.heavy_count > 0) {
+    int32_t* scratch = nullptr;
+    if (R.heavy_scratch > 0) {
+      scratch = (int32_t*)dev_alloc(4 * R.heavy_scratch, st);
+      if (!scratch) return fail(CG_ERR_OOM, "device allocation failed (row sort scratch)");
+    }
+    const size_t smem = 4 * kSmemSortCap;
+    row_sort_kernel<<<grid_for(R.heavy_count, 1, 152 * 4), 512, smem, st>>>(
+        R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch);
+    e = cudaGetLastError();
+    if (scratch) dev_free(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "row sort");
+  }
+  return CG_OK;
+}
+
+}  // namespace cg
