@@ -84,6 +84,10 @@ const char* cg_last_error(void);
 /* Library version string. */
 const char* cg_version(void);
 
+/* Number of CUDA kernels the library has launched in this process so far
+   (all threads and devices); a diagnostic for launch accounting. */
+uint64_t cg_launch_count(void);
+
 /*
  * cg_build -- index n points (Section 3: bounding box p-/p+ of Section 3.1,
  * grid size n_a = floor((p+_a - p-_a)/s_a) + 1 of Eq. grid-size, voxel of a

@@ -27,7 +27,7 @@ FP64, FP32_OFFSET = 0, 1
 STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4: "CG_ERR_TIMEOUT",
           5: "CG_ERR_OVERFLOW", 6: "CG_ERR_INTERNAL", 7: "CG_ERR_UNIMPLEMENTED"}
 
-EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_build", "cg_build_batched",
+EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count", "cg_build", "cg_build_batched",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
            "cg_all_points_knn"]
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_set_allocator": [P, P, P],
             "cg_last_error": [],
             "cg_version": [],
+            "cg_launch_count": [],
             "cg_build": [P, I64, D, D, I, I, I, P, P],
             "cg_build_batched": [P, P, I32, P, I, I, I, P, P],
             "cg_index_info": [P, P],
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_char_p if name in ("cg_last_error", "cg_version") else ctypes.c_int
+        lib.cg_launch_count.restype = ctypes.c_uint64
         _lib = lib
         return lib
 
@@ -126,6 +128,11 @@ def _points(x: torch.Tensor) -> torch.Tensor:
 
 def cg_version() -> str:
     return load().cg_version().decode()
+
+
+def cg_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().cg_launch_count())
 
 
 def cg_build(xyz: torch.Tensor, cell_xy: float, cell_z: float | None = None, dim: int = 2,

@@ -302,10 +302,10 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_ALLOC(toff_dev, int64_t, ntiles + 1, tmp);
   CG_ALLOC(bb, unsigned long long, 6 * ntiles, tmp);
   CG_CUDA(cudaMemcpyAsync(toff_dev, toff_host, sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
-  bbox_init_kernel<<<(6 * ntiles + 255) / 256, 256, 0, st>>>(bb, ntiles);
+  bbox_init_kernel<<<(6 * ntiles + 255) / 256, 256, 0, st>>>(bb, ntiles); note_launch();
   {
     int64_t blocks = (n + kThreads * kBoxItems - 1) / (kThreads * kBoxItems);
-    bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, toff_dev, ntiles, bb, ix->status);
+    bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, toff_dev, ntiles, bb, ix->status); note_launch();
   }
   CG_CUDA(cudaGetLastError());
   std::vector<unsigned long long> bbh(6 * ntiles);
@@ -371,7 +371,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_ALLOC(keys, uint32_t, n, tmp);
   CG_ALLOC(skeys, uint32_t, n, tmp);
   CG_ALLOC(perm, uint32_t, n, tmp);
-  key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, ntiles, dim, keys);
+  key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, ntiles, dim, keys); note_launch();
   CG_CUDA(cudaGetLastError());
 
   // B3: stable radix sort of (key, id)
@@ -387,7 +387,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   if (precision == CG_FP32_OFFSET) CG_ALLOC(ix->pts32, float4, n, ix->bufs);
   else CG_ALLOC(ix->pts64s, double4_32a, n, ix->bufs);
   gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, perm, skeys, ix->tiles, ntiles,
-                                                             ix->pts32, ix->pts64s);
+                                                             ix->pts32, ix->pts64s); note_launch();
   CG_CUDA(cudaGetLastError());
 
   // runs of equal keys: the sorted unique-key table
@@ -396,7 +396,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_ALLOC(rank, uint32_t, n + 1, tmp);
   void* scan_scratch;
   CG_ALLOC(scan_scratch, char, scan_scratch_bytes(std::max<int64_t>(n, key_base + 1)), tmp);
-  run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag);
+  run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag); note_launch();
   CG_CUDA(exclusive_scan_u32_u32(flag, rank, n, scan_scratch, ix->status, st));
   uint32_t m = 0;
   CG_CUDA(cudaMemcpyAsync(&m, rank + n, 4, cudaMemcpyDeviceToHost, st));
@@ -404,17 +404,17 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   ix->nkeys = m;
   CG_ALLOC(ix->ukeys, uint32_t, m, ix->bufs);
   CG_ALLOC(ix->ustart, uint32_t, m + 1, ix->bufs);
-  run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag, rank, ix->ukeys, ix->ustart);
+  run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag, rank, ix->ukeys, ix->ustart); note_launch();
   CG_CUDA(cudaGetLastError());
   CG_CUDA(cudaMemsetAsync(ix->scratch_u32, 0, 4, st));
-  max_run_kernel<<<grid_for(m, kThreads, 152 * 4), kThreads, 0, st>>>(ix->ustart, m, ix->scratch_u32);
+  max_run_kernel<<<grid_for(m, kThreads, 152 * 4), kThreads, 0, st>>>(ix->ustart, m, ix->scratch_u32); note_launch();
 
   if (flavor == CG_DENSE) {
     uint32_t* cnt;
     CG_ALLOC(cnt, uint32_t, key_base, tmp);
     CG_ALLOC(ix->cstart, uint32_t, key_base + 1, ix->bufs);
     CG_CUDA(cudaMemsetAsync(cnt, 0, 4 * key_base, st));
-    voxel_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, m, cnt);
+    voxel_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, m, cnt); note_launch();
     CG_CUDA(exclusive_scan_u32_u32(cnt, ix->cstart, (int64_t)key_base, scan_scratch, ix->status, st));
     ix->dense_slices = ntiles;
   } else {
@@ -423,13 +423,13 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
     CG_ALLOC(ix->hash, unsigned long long, cap, ix->bufs);
     CG_CUDA(cudaMemsetAsync(ix->hash, 0xff, 8ull * cap, st));
     hash_insert_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, m, ix->hash, ix->hash_mask,
-                                                                   ix->status);
+                                                                   ix->status); note_launch();
     CG_CUDA(cudaGetLastError());
     if (flavor == CG_MIXED) {
       uint32_t* ne;
       CG_ALLOC(ne, uint32_t, slice_base, tmp);
       CG_CUDA(cudaMemsetAsync(ne, 0, 4 * slice_base, st));
-      slice_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, m, ix->tiles, ntiles, dim, ne);
+      slice_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, m, ix->tiles, ntiles, dim, ne); note_launch();
       std::vector<uint32_t> neh(slice_base);
       CG_CUDA(cudaMemcpyAsync(neh.data(), ne, 4 * slice_base, cudaMemcpyDeviceToHost, st));
       CG_CUDA(cudaStreamSynchronize(st));
@@ -455,7 +455,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
       CG_CUDA(cudaMemsetAsync(ix->mtab, 0, 8 * std::max<uint64_t>(tab, 1), st));
       mixed_fill_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, m, ix->tiles,
                                                                     ntiles, dim, ix->slice_dense,
-                                                                    ix->slice_tab_off, ix->mtab);
+                                                                    ix->slice_tab_off, ix->mtab); note_launch();
       CG_CUDA(cudaGetLastError());
     }
   }

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,7 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
                    double* d2, cudaStream_t st);
 
 namespace {
+std::atomic<unsigned long long> g_launches{0};
 thread_local std::string g_last_error;
 cg_alloc_fn g_alloc = nullptr;
 cg_free_fn g_free = nullptr;
@@ -29,6 +31,8 @@ void* g_user = nullptr;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 cg_status fail(cg_status s, const std::string& msg) {
   g_last_error = msg;
@@ -95,6 +99,8 @@ cg_status cg_set_allocator(cg_alloc_fn alloc_fn, cg_free_fn free_fn, void* user)
 const char* cg_last_error(void) { return g_last_error.c_str(); }
 
 const char* cg_version(void) { return "cheesegpu 0.1 (sm_103a)"; }
+
+uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 cg_status cg_build(const double* xyz_dev, int64_t n, double cell_xy, double cell_z, int dim,
                    cg_flavor flavor, cg_precision precision, void* stream, cg_index_t* out) {

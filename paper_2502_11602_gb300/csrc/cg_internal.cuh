@@ -44,6 +44,9 @@ enum : uint32_t {
 // most on a GB300 before the wait is abandoned with ST_TIMEOUT.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+// Counts kernel launches made by the library (host side, diagnostics).
+void note_launch(int n = 1);
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;

@@ -632,17 +632,17 @@ cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_
   cudaError_t e = cudaMemsetAsync(P.nblocks_dev, 0, 64, st);
   if (nq > 0) {
     query_key_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, ix->tiles, ix->dim, keys,
-                                                         P.nblocks_dev + 4, ix->status);
+                                                         P.nblocks_dev + 4, ix->status); note_launch();
     const Tile& T = ix->tiles_host[0];
     int bits = 0;
     uint64_t kmax = (uint64_t)T.key_base + (uint64_t)T.n[0] * T.n[1] * T.n[2];
     while (bits < 32 && ((uint64_t)1 << bits) < kmax) ++bits;
     if (e == cudaSuccess) e = radix_sort_pairs(keys, nq, bits, skeys, perm, sort_scratch, ix->status, st);
-    query_gather_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, perm, ix->tiles, P.qrec, P.qrec64);
-    qrun_flag_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag);
+    query_gather_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, perm, ix->tiles, P.qrec, P.qrec64); note_launch();
+    qrun_flag_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag); note_launch();
     if (e == cudaSuccess) e = exclusive_scan_u32_u32(flag, rank, nq, scan_scratch, ix->status, st);
     qrun_emit_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag, rank, P.blk_key, P.blk_beg,
-                                                        P.nblocks_dev);
+                                                        P.nblocks_dev); note_launch();
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   tmp.release(st);
@@ -669,7 +669,7 @@ cudaError_t launch_radius(const RadiusLaunch& L, uint32_t* counts, const int64_t
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = true;
   }
-  kern<<<grid, RT, smem, st>>>(L.iv, L.qs, L.thr, counts, offsets, out, heavy, work_ctr, status);
+  kern<<<grid, RT, smem, st>>>(L.iv, L.qs, L.thr, counts, offsets, out, heavy, work_ctr, status); note_launch();
   return cudaGetLastError();
 }
 
@@ -744,7 +744,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
       static_assert(sizeof(th) <= sizeof(R.thr_host), "threshold copy");
       memcpy(R.thr_host, &th, sizeof th);
     } else {
-      thresholds_kernel<<<1, 1, 0, st>>>(R.thr, r, emax, ix->plan.nblocks_dev + 4);
+      thresholds_kernel<<<1, 1, 0, st>>>(R.thr, r, emax, ix->plan.nblocks_dev + 4); note_launch();
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(e, "thresholds");
@@ -851,7 +851,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     }
     const size_t smem = 4 * kSmemSortCap;
     row_sort_kernel<<<grid_for(R.heavy_count, 1, 152 * 4), 512, smem, st>>>(
-        R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch);
+        R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch); note_launch();
     e = cudaGetLastError();
     if (scratch) dev_free(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "row sort");

@@ -311,7 +311,7 @@ static cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, void* scratch,
   unsigned long long* status = (unsigned long long*)((char*)scratch + 256);
   cudaError_t e = cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), st);
   if (e != cudaSuccess) return e;
-  scan_kernel<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, status, ctr, err);
+  scan_kernel<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, status, ctr, err); note_launch();
   return cudaGetLastError();
 }
 
@@ -340,7 +340,7 @@ cudaError_t radix_sort_pairs(const uint32_t* keys, int64_t n, int key_bits, uint
   if (passes == 0) {
     cudaError_t e = cudaMemcpyAsync(keys_sorted, keys, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    iota_kernel<<<grid_for(n, 256), 256, 0, st>>>(vals_sorted, n);
+    iota_kernel<<<grid_for(n, 256), 256, 0, st>>>(vals_sorted, n); note_launch();
     return cudaGetLastError();
   }
   int64_t tiles = (n + kSortTile - 1) / kSortTile;
@@ -356,8 +356,8 @@ cudaError_t radix_sort_pairs(const uint32_t* keys, int64_t n, int key_bits, uint
 
   cudaError_t e = cudaMemsetAsync(hist, 0, 4 * kRadix * 4 + 256, st);
   if (e != cudaSuccess) return e;
-  radix_hist_kernel<<<grid_for(n, kSortThreads, 152 * 4), kSortThreads, 0, st>>>(keys, n, passes, hist);
-  radix_hist_scan_kernel<<<1, kRadix, 0, st>>>(hist, passes);
+  radix_hist_kernel<<<grid_for(n, kSortThreads, 152 * 4), kSortThreads, 0, st>>>(keys, n, passes, hist); note_launch();
+  radix_hist_scan_kernel<<<1, kRadix, 0, st>>>(hist, passes); note_launch();
   const uint32_t* kin = keys;
   const uint32_t* vin = nullptr;
   for (int pass = 0; pass < passes; ++pass) {
@@ -368,7 +368,7 @@ cudaError_t radix_sort_pairs(const uint32_t* keys, int64_t n, int key_bits, uint
     if (e != cudaSuccess) return e;
     onesweep_kernel<<<(unsigned)tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, n, 8 * pass,
                                                              hist + pass * kRadix, status,
-                                                             ctrs + pass, err);
+                                                             ctrs + pass, err); note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     kin = kout;

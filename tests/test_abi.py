@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ch
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:cg_status|const char\*)\s+(cg_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:cg_status|const char\*|uint64_t)\s+(cg_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_library_builds_and_exports_header_symbols():
