@@ -218,6 +218,37 @@ cg_status cg_knn(cg_index_t index, const double* q_dev, int64_t nq, int32_t k, i
 cg_status cg_all_points_knn(cg_index_t index, int32_t k, int32_t* idx_dev, double* d2_dev,
                             void* stream);
 
+/*
+ * cg_offsets_scan_noalloc -- the exclusive scan that turns per-query
+ * neighbour counts into CSR offsets, without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate, e.g. a serving loop whose device memory was reserved up
+ * front by another allocator, a real-time path where an allocation could
+ * block or fail, or a host that gives the library nothing but the input and
+ * output buffers it owns.  The regular count pass allocates its scan
+ * scratch; this call uses a fixed array compiled into the library instead.
+ *
+ *  counts_dev   device uint32 [n] per-query counts (read).
+ *  n            0 <= n <= 134217728 (2^27); larger n is rejected with
+ *               CG_ERR_INVALID before any device work.
+ *  offsets_dev  device int64 [n+1], written: offsets[0] = 0,
+ *               offsets[i+1] = offsets[i] + counts[i].  If a bounded device
+ *               wait gives up, offsets[n] is set to -1 (the other entries are
+ *               then unreliable); this never happens unless the GPU is shared
+ *               so heavily that a resident block cannot make progress.
+ *  stream       the call is asynchronous on this stream.
+ * Scratch: 512 KiB + 256 B in a file-scope device array that every GPU which
+ * loads the library holds until the process exits.  It is shared by all
+ * calls: calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other's result; serialise them.  Each call clears
+ * the part it uses before its kernel runs.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current and caches it; make that first call before any stream capture.
+ * The call makes no cudaMalloc, cudaFree or other allocating call.
+ */
+cg_status cg_offsets_scan_noalloc(const uint32_t* counts_dev, int64_t n, int64_t* offsets_dev,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

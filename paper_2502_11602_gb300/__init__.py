@@ -30,7 +30,7 @@ STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4:
 EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count", "cg_build", "cg_build_batched",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
-           "cg_all_points_knn"]
+           "cg_all_points_knn", "cg_offsets_scan_noalloc"]
 
 
 class CheeseError(RuntimeError):
@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_all_points_fill": [P, D, I, P, P, P],
             "cg_knn": [P, P, I64, I32, P, P, P],
             "cg_all_points_knn": [P, I32, P, P, P],
+            "cg_offsets_scan_noalloc": [P, I64, P, P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
