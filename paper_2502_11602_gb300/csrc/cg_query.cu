@@ -33,77 +33,6 @@
 
 namespace cg {
 
-// ----------------------------------------------------------------- thresholds
-
-namespace {
-__host__ __device__ inline float f_down(double x) {
-#ifdef __CUDA_ARCH__
-  return __double2float_rd(x);
-#else
-  float f = (float)x;
-  if ((double)f > x) f = nextafterf(f, -INFINITY);
-  return f;
-#endif
-}
-__host__ __device__ inline float f_up(double x) {
-#ifdef __CUDA_ARCH__
-  return __double2float_ru(x);
-#else
-  float f = (float)x;
-  if ((double)f < x) f = nextafterf(f, INFINITY);
-  return f;
-#endif
-}
-}  // namespace
-
-// Binary32 offset test, error model.  Per axis the binary32 difference
-// dxf = fl32(x~_p - x~_c) and the exact dx = fl64(p - c) satisfy
-//   |dxf - dx| <= alpha + beta |dx|,  alpha = (e_p + e_q)(1 + u),
-//   beta = (u + U)(1 + 2U),  u = 2^-24, U = 2^-53,
-// where e_p, e_q bound |x~ - (x - O)| (binary32 rounding of the offset plus
-// the binary64 rounding of x - O).  With S = sum dx^2 and Sf = sum dxf^2:
-//   |Sf - S| <= c1 sqrt(S) + c0 + c2 S,  c1 = 2 alpha (1 + beta) sqrt(3),
-//   c0 = 3 alpha^2, c2 = 2 beta + beta^2 (Cauchy-Schwarz on the three axes).
-// The binary32 value d2f is within 3.0000002 u Sf of Sf (three roundings) and
-// the binary64 value d2 within 3.0000001 U S of S.  Hence
-//   d2f <= T_lo  =>  d2 <= r2     T_lo = (S_in (1 - c2) - c1 sqrt(S_in) - c0)(1 - 3.0000002u)
-//   d2f >  T_hi  =>  d2 >  r2     T_hi = (S_mx (1 + c2) + c1 sqrt(S_mx) + c0)(1 + 3.0000002u)
-// with S_in = r2 (1 - 4U), S_mx = r2 (1 + 4U); the margins are doubled for
-// headroom.  The cube uses the same argument on each axis alone.
-__host__ __device__ Thresholds make_thresholds(double r, double e_p, double e_q) {
-  const double u = 5.9604644775390625e-08;   // 2^-24
-  const double U = 1.1102230246251565e-16;   // 2^-53
-  Thresholds t;
-  t.r2 = r * r;
-  const double r2 = t.r2;
-  const double alpha = (e_p + e_q) * (1.0 + u);
-  const double beta = (u + U) * (1.0 + 2.0 * U);
-  const double c1 = 2.0 * alpha * (1.0 + beta) * 1.7320508075688774;
-  const double c0 = 3.0 * alpha * alpha;
-  const double c2 = 2.0 * beta + beta * beta;
-  const double s_in = r2 * (1.0 - 4.0 * U);
-  const double s_mx = r2 * (1.0 + 4.0 * U);
-  double t_lo = (s_in * (1.0 - c2) - c1 * sqrt(s_in) - c0) * (1.0 - 3.0000002 * u);
-  double t_hi = (s_mx * (1.0 + c2) + c1 * sqrt(s_mx) + c0) * (1.0 + 3.0000002 * u);
-  t_lo = r2 - 2.0 * (r2 - t_lo);
-  t_hi = r2 + 2.0 * (t_hi - r2);
-  t.s_lo = t_lo > 0 ? f_down(t_lo) : -1.0f;
-  t.s_hi = f_up(t_hi);
-  // cube: one axis, |dx| <= r (1 + U) when fl64(dx^2) <= r2
-  const double rin = sqrt(r2 * (1.0 - 2.0 * U)) * (1.0 - beta) - alpha;
-  double c_lo = rin > 0 ? (1.0 - 1.0000001 * u) * rin * rin : -1.0;
-  const double rmx = sqrt(r2 * (1.0 + 2.0 * U)) * (1.0 + beta) + alpha;
-  double c_hi = (1.0 + 1.0000001 * u) * rmx * rmx;
-  c_lo = r2 - 2.0 * (r2 - c_lo);
-  c_hi = r2 + 2.0 * (c_hi - r2);
-  t.c_lo = c_lo > 0 ? f_down(c_lo) : -1.0f;
-  t.c_hi = f_up(c_hi);
-  t.r_f = f_up(r);
-  t.e_q = f_up(e_q);
-  t.pad_[0] = t.pad_[1] = 0.f;
-  return t;
-}
-
 namespace {
 
 constexpr int RT = 256;         // threads per CTA
