@@ -370,7 +370,8 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   uint32_t *keys, *skeys, *perm;
   CG_ALLOC(keys, uint32_t, n, tmp);
   CG_ALLOC(skeys, uint32_t, n, tmp);
-  CG_ALLOC(perm, uint32_t, n, tmp);
+  CG_ALLOC(perm, uint32_t, n, ix->bufs);  // kept: original id of every sorted position
+  ix->sid = perm;
   key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, ntiles, dim, keys); note_launch();
   CG_CUDA(cudaGetLastError());
 

@@ -44,9 +44,28 @@ cg_status cuda_fail(cudaError_t e, const char* what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Keeps freed memory in the device's default stream-ordered pool across
+// synchronisations (the default threshold of 0 hands it back to the driver
+// at every sync, and re-mapping gigabytes costs milliseconds per call).
+static void keep_pool_warm() {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  const uint64_t bit = 1ull << dev;
+  if (done_mask.load() & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t threshold = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  cudaGetLastError();
+  done_mask.fetch_or(bit);
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
   if (g_alloc) return g_alloc(bytes, (void*)st, g_user);
+  keep_pool_warm();
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
     cudaGetLastError();

@@ -37,6 +37,7 @@ struct DevBufs {
 };
 
 struct Thresholds;
+struct BlockPlan;
 
 // Cached plan of an external query set (query order, blocks, records).
 struct QueryPlan {
@@ -71,6 +72,11 @@ struct RadiusState {
   uint32_t heavy_count = 0;
   uint64_t heavy_scratch = 0;
   char thr_host[64];
+  // fast kernels: per-group plans, mask / id layouts and the large groups
+  struct BlockPlan* plans = nullptr;
+  uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
+  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr, *meta = nullptr;
+  uint32_t big_n = 0;
 };
 
 }  // namespace cg
@@ -87,6 +93,7 @@ struct cg_index {
   double* xyz64 = nullptr;
   uint32_t* ukeys = nullptr;
   uint32_t* ustart = nullptr;
+  uint32_t* sid = nullptr;       // [n] original id of every sorted position
   uint32_t nkeys = 0;
   uint32_t* cstart = nullptr;
   unsigned long long* hash = nullptr;
@@ -113,6 +120,7 @@ struct cg_index {
     v.nkeys = nkeys;
     v.pts32 = pts32;
     v.pts64s = pts64s;
+    v.sid = sid;
     v.xyz64 = xyz64;
     v.ukeys = ukeys;
     v.ustart = ustart;

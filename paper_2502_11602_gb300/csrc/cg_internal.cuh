@@ -111,6 +111,7 @@ struct IndexView {
   const float4* pts32;     // [n] sorted: x~, y~, z~, id bits (binary32 path)
   const double4_32a* pts64s;   // [n] sorted: x, y, z, id bits (binary64 path)
   const double* xyz64;     // [n][3] original order (exact rechecks)
+  const uint32_t* sid;     // [n] original id of every sorted position
   const uint32_t* ukeys;   // [nkeys] sorted unique voxel keys
   const uint32_t* ustart;  // [nkeys+1] start of each run in sorted order
   const uint32_t* cstart;  // dense: [ncell+1]

@@ -174,8 +174,15 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
   for (;;) {
     if (threadIdx.x == 0) s_blk = atomicAdd(work_ctr, 1u);
     __syncthreads();
-    const uint32_t b = s_blk;
-    if (b >= qs.nblocks) break;
+    const uint32_t wi = s_blk;
+    uint32_t b;
+    if (qs.blk_list) {  // only the listed blocks (groups too large for the fast kernels)
+      if (wi >= *qs.blk_list_n) break;
+      b = qs.blk_list[wi];
+    } else {
+      if (wi >= qs.nblocks) break;
+      b = wi;
+    }
     const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
     const uint32_t bkey = qs.blk_key[b];
     const int ti = ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey);
@@ -731,10 +738,61 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
   }
   const int grid = radius_grid(ix->precision);
   if (nqq > 0 && L.qs.nblocks > 0) {
+    const uint32_t nb = L.qs.nblocks;
+    // groups too large for the fast kernels go through the general CTA kernel
+    RadiusLaunch Lbig = L;
+    Lbig.qs.blk_list = R.big_list;
+    Lbig.qs.blk_list_n = R.ctrs + 12;
     if (!fill) {
-      e = dispatch_radius<false>(ix->precision, kernel, L, R.counts, nullptr, nullptr, H, work, ix->status, grid, st);
+      R.plans = (BlockPlan*)R.bufs.get(sizeof(BlockPlan) * (size_t)nb, st);
+      R.msize = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
+      R.isize = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
+      R.moff = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
+      R.idoff = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
+      R.big_list = (uint32_t*)R.bufs.get(4 * (size_t)nb, st);
+      void* sscr = R.bufs.get(scan_scratch_bytes(nb), st);
+      if (!R.plans || !R.msize || !R.isize || !R.moff || !R.idoff || !R.big_list || !sscr)
+        return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
+      Lbig.qs.blk_list = R.big_list;
+      e = launch_radius_plan(ix->precision, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
+                             R.ctrs + 12, st);
+      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, ix->status, st);
+      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, ix->status, st);
+      uint32_t tots[3] = {0, 0, 0};
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[0], R.moff + nb, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[1], R.idoff + nb, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[2], R.ctrs + 12, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "radius plan");
+      R.masks = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[0], 1), st);
+      R.ids = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[1], 1), st);
+      if (!R.masks || !R.ids) return fail(CG_ERR_OOM, "device allocation failed (radius masks)");
+      R.big_n = tots[2];
+      if (ix->precision == CG_FP32_OFFSET) {
+        R.meta = (uint32_t*)R.bufs.get(16 * (size_t)nb, st);
+        if (!R.meta) return fail(CG_ERR_OOM, "device allocation failed (radius meta)");
+        e = launch_radius_count3(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks, R.ids,
+                                 R.meta, R.ctrs + 14, ix->status, st);
+      } else {
+        e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
+                                 R.masks, R.ids, R.ctrs + 14, ix->status, st);
+      }
+      if (e == cudaSuccess && R.big_n > 0)
+        e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, ix->status,
+                                   grid, st);
     } else {
-      e = dispatch_radius<true>(ix->precision, kernel, L, nullptr, offsets, out, H, work, ix->status, grid, st);
+      e = cudaMemsetAsync(R.ctrs + 16, 0, 4, st);
+      if (e == cudaSuccess) {
+        if (ix->precision == CG_FP32_OFFSET)
+          e = launch_radius_fill3(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, R.meta, offsets, out,
+                                  R.ctrs + 16, st);
+        else
+          e = launch_radius_fill2(ix->precision, L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets,
+                                  out, R.ctrs + 16, st);
+      }
+      if (e == cudaSuccess && R.big_n > 0)
+        e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, ix->status, grid,
+                                  st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "radius kernel");
   }

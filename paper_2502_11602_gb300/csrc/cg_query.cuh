@@ -99,7 +99,43 @@ struct QuerySet {
   const float4* qrec;          // [nq] x~, y~, z~, id bits (binary32)
   const double4_32a* qrec64;       // [nq] x, y, z, id bits (binary64)
   const double* q64;           // [nq][3] original order, exact coordinates
+  const uint32_t* blk_list = nullptr;    // optional subset of blocks to process
+  const uint32_t* blk_list_n = nullptr;  // its length (device)
 };
+
+// Per voxel group: what the fast radius kernels need (see cg_radius2.cu).
+constexpr int kPlanSpans = 32;  // non-empty voxel runs per group
+struct BlockPlan {
+  uint32_t q0, nq;       // queries [q0, q0 + nq) in query order
+  uint32_t K;            // staged candidates (sum of span lengths)
+  uint16_t nsp, W;       // spans, 32-bit mask words per query
+  uint32_t heavy;        // 1: handled by the general CTA kernel
+  uint32_t pad_[3];
+  uint32_t start[kPlanSpans];
+  uint32_t len[kPlanSpans];
+};
+
+// Fast radius kernels (cg_radius2.cu).
+cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
+                               BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
+                               uint32_t* big_n, cudaStream_t st);
+cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
+                                 const Thresholds* thr, const BlockPlan* plans, const uint32_t* moff,
+                                 const uint32_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
+                                 unsigned* work, uint32_t* status, cudaStream_t st);
+cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
+                                const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
+                                cudaStream_t st);
+
+cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
+                                 const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
+                                 uint32_t* counts, uint32_t* masks, uint32_t* ids, uint32_t* meta,
+                                 unsigned* work, uint32_t* status, cudaStream_t st);
+cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
+                                const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
+                                unsigned* work, cudaStream_t st);
 
 // Builds (or reuses) the plan of an external query set on ix->plan.
 cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st);

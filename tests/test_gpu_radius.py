@@ -157,3 +157,20 @@ def test_als_12m_tile_sampled_parity():
         for j in g_ind[g_off[q]:g_off[q + 1]][:50]:
             assert q in set(g_ind[g_off[j]:g_off[j + 1]].tolist())
     ix.close()
+
+
+@pytest.mark.parametrize("kernel", [cg.SPHERE, cg.CUBE])
+def test_tall_columns_and_stacked_layers(kernel):
+    # vertical structures spanning > 32 search radii in z (z-groups wider
+    # than r), stacked ground / roof layers and points below the origin
+    rng = np.random.default_rng(10)
+    n = 30_000
+    ground = np.stack([rng.uniform(0, 30, n), rng.uniform(0, 30, n), rng.normal(-3.0, 0.05, n)], 1)
+    roof = np.stack([rng.uniform(5, 15, n // 2), rng.uniform(5, 15, n // 2), rng.normal(12.0, 0.05, n // 2)], 1)
+    poles = []
+    for px, py in rng.uniform(0, 30, (40, 2)):
+        m = 800
+        poles.append(np.stack([px + rng.normal(0, 0.05, m), py + rng.normal(0, 0.05, m), rng.uniform(-3, 120, m)], 1))
+    xyz = np.ascontiguousarray(np.concatenate([ground, roof] + poles) + [508000.0, 5440000.0, 0.0])
+    for r in (0.4, 1.0, 2.5):
+        _check(xyz, None, r, 1.0, kernel=kernel)
