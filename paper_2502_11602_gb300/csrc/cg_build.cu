@@ -181,16 +181,59 @@ __global__ void run_flag_kernel(const uint32_t* __restrict__ skeys, int64_t n,
 // runs: ukeys[r] = key, ustart[r] = first sorted position; ustart[m] = n
 __global__ void run_emit_kernel(const uint32_t* __restrict__ skeys, int64_t n,
                                 const uint32_t* __restrict__ flag, const uint32_t* __restrict__ rank,
-                                uint32_t* __restrict__ ukeys, uint32_t* __restrict__ ustart) {
+                                uint32_t* __restrict__ ukeys, uint32_t* __restrict__ ustart, uint32_t cap) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (flag[i]) {
       uint32_t r = rank[i];
-      ukeys[r] = skeys[i];
-      ustart[r] = (uint32_t)i;
+      if (r < cap) {  // a replay whose data grew more runs is flagged, never overruns
+        ukeys[r] = skeys[i];
+        ustart[r] = (uint32_t)i;
+      }
     }
-    if (i == n - 1) ustart[rank[n]] = (uint32_t)n;
+    if (i == n - 1 && rank[n] <= cap) ustart[rank[n]] = (uint32_t)n;
   }
+}
+
+// --- replay support -------------------------------------------------------
+
+// Recomputes every tile's box, origin and error bounds from the reduced
+// bounding boxes (the host formulas of build_index, in binary64 without
+// contraction); a grid size that differs from the captured one flags a
+// re-plan instead of changing the key layout.
+__global__ void tiles_refresh_kernel(Tile* tiles, int ntiles, const unsigned long long* __restrict__ bb, int dim,
+                                     uint32_t* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  Tile& T = tiles[t];
+  double M = 0.0, ext = 0.0;
+  int64_t nmax = 1;
+  bool same = true;
+  for (int a = 0; a < 3; ++a) {
+    const double lo = ord_to_dbl(bb[6 * t + a]), hi = ord_to_dbl(bb[6 * t + 3 + a]);
+    const double w = __dsub_rn(hi, lo);
+    int64_t na = (int64_t)floor(__ddiv_rn(w, T.s[a])) + 1;
+    if (dim == 2 && a == 2) na = 1;
+    same &= na == (int64_t)T.n[a];
+    nmax = max(nmax, na);
+    T.lo[a] = lo;
+    T.hi[a] = hi;
+    const double o = __dadd_rn(lo, __dmul_rn(0.5, w));
+    T.origin[a] = o;
+    M = fmax(M, fmax(fabs(__dsub_rn(hi, o)), fabs(__dsub_rn(o, lo))));
+    T.D[a] = __double2float_rn(__dsub_rn(o, lo));
+    ext = fmax(ext, w);
+  }
+  M = __dmul_rn(M, 1.0 + 1e-12);
+  const double enc = __dadd_rn(__dmul_rn(ldexp(M, -24), 1.0 + 1e-6), ldexp(M, -52));
+  T.enc_err = __double2float_ru(enc);
+  const double smin = fmin(T.s[0], fmin(T.s[1], T.s[2]));
+  T.eta = __double2float_ru(4.0 * ((enc + ldexp(3.0 * ext + 2.0 * M, -24)) / smin + ldexp((double)nmax + 2.0, -22)) + 1e-6);
+  if (!same) atomicOr(status, ST_REPLAN);
+}
+
+__global__ void count_check_kernel(const uint32_t* __restrict__ value, uint32_t expected, uint32_t* status) {
+  if (*value != expected) atomicOr(status, ST_REPLAN);
 }
 
 __global__ void voxel_count_kernel(const uint32_t* __restrict__ ukeys,
@@ -405,7 +448,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   ix->nkeys = m;
   CG_ALLOC(ix->ukeys, uint32_t, m, ix->bufs);
   CG_ALLOC(ix->ustart, uint32_t, m + 1, ix->bufs);
-  run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag, rank, ix->ukeys, ix->ustart); note_launch();
+  run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag, rank, ix->ukeys, ix->ustart, m); note_launch();
   CG_CUDA(cudaGetLastError());
   CG_CUDA(cudaMemsetAsync(ix->scratch_u32, 0, 4, st));
   max_run_kernel<<<grid_for(m, kThreads, 152 * 4), kThreads, 0, st>>>(ix->ustart, m, ix->scratch_u32); note_launch();
@@ -472,6 +515,69 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   return CG_OK;
 #undef CG_ALLOC
 #undef CG_CUDA
+}
+
+
+// Buffers a replayed build needs besides the index's own (kept for the
+// lifetime of a captured pipeline).
+cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st) {
+  const int64_t n = ix->n;
+  w.keys = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.skeys = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.flag = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.rank = (uint32_t*)w.bufs.get(4 * (size_t)(n + 1), st);
+  w.cnt = (uint32_t*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->ncell, 1), st);
+  w.sort_scr = w.bufs.get(radix_sort_scratch_bytes(n), st);
+  w.scan_scr = w.bufs.get(scan_scratch_bytes(std::max<int64_t>(n, ix->ncell + 1)), st);
+  w.bb = (unsigned long long*)w.bufs.get(8 * 6 * (size_t)ix->ntiles, st);
+  w.toff = (int64_t*)w.bufs.get(8 * (size_t)(ix->ntiles + 1), st);
+  if (!w.keys || !w.skeys || !w.flag || !w.rank || !w.cnt || !w.sort_scr || !w.scan_scr || !w.bb || !w.toff)
+    return fail(CG_ERR_OOM, "device allocation failed (pipeline build work)");
+  std::vector<int64_t> toff(ix->ntiles + 1);
+  for (int t = 0; t < ix->ntiles; ++t) toff[t] = ix->tiles_host[t].pt_base;
+  toff[ix->ntiles] = n;
+  cudaError_t e = cudaMemcpyAsync(w.toff, toff.data(), 8 * toff.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "pipeline build work");
+  int bits = 0;
+  while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)ix->ncell) ++bits;
+  w.bits = bits;
+  w.nkeys = ix->nkeys;
+  return CG_OK;
+}
+
+// The dense build again, into the index's existing buffers, with no host
+// synchronisation and no allocation (so it can be captured in a graph).
+cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st) {
+  if (ix->flavor != CG_DENSE) return fail(CG_ERR_UNIMPLEMENTED, "pipeline replay needs the dense flavour");
+  const int64_t n = ix->n;
+  const int T = ix->ntiles;
+  cudaError_t e;
+  bbox_init_kernel<<<(6 * T + 255) / 256, 256, 0, st>>>(w.bb, T); note_launch();
+  {
+    int64_t blocks = (n + kThreads * kBoxItems - 1) / (kThreads * kBoxItems);
+    bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, w.toff, T, w.bb, ix->status); note_launch();
+  }
+  tiles_refresh_kernel<<<(T + 127) / 128, 128, 0, st>>>(ix->tiles, T, w.bb, ix->dim, ix->status); note_launch();
+  key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, T, ix->dim, w.keys); note_launch();
+  e = radix_sort_pairs(w.keys, n, w.bits, w.skeys, ix->sid, w.sort_scr, ix->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay sort");
+  gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->sid, w.skeys, ix->tiles, T, ix->pts32,
+                                                             ix->pts64s); note_launch();
+  e = cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay copy");
+  run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag); note_launch();
+  e = exclusive_scan_u32_u32(w.flag, w.rank, n, w.scan_scr, ix->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay scan");
+  run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag, w.rank, ix->ukeys, ix->ustart,
+                                                               w.nkeys); note_launch();
+  count_check_kernel<<<1, 1, 0, st>>>(w.rank + n, w.nkeys, ix->status); note_launch();
+  e = cudaMemsetAsync(w.cnt, 0, 4 * (size_t)ix->ncell, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay memset");
+  voxel_count_kernel<<<grid_for(w.nkeys, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, w.nkeys, w.cnt); note_launch();
+  e = exclusive_scan_u32_u32(w.cnt, ix->cstart, ix->ncell, w.scan_scr, ix->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay cell starts");
+  return CG_OK;
 }
 
 }  // namespace cg

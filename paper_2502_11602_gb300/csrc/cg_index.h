@@ -79,6 +79,17 @@ struct RadiusState {
   uint32_t big_n = 0;
 };
 
+// Workspace of a replayed (graph-captured) build.
+struct BuildWork {
+  DevBufs bufs;
+  uint32_t *keys = nullptr, *skeys = nullptr, *flag = nullptr, *rank = nullptr, *cnt = nullptr;
+  void *sort_scr = nullptr, *scan_scr = nullptr;
+  unsigned long long* bb = nullptr;
+  int64_t* toff = nullptr;
+  int bits = 0;
+  uint32_t nkeys = 0;
+};
+
 }  // namespace cg
 
 struct cg_index {
@@ -137,4 +148,6 @@ struct cg_index {
 namespace cg {
 // Reads and clears the device status word (synchronises the stream).
 cg_status check_status(cg_index* ix, cudaStream_t st);
+cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
+cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
 }  // namespace cg

@@ -38,7 +38,14 @@ enum : uint32_t {
   ST_OVERFLOW = 4u,    // an output capacity was exceeded
   ST_INTERNAL = 8u,    // a consistency check failed
   ST_KNN_SLOW = 16u,   // some k-NN queries need the slow path (not an error)
+  ST_REPLAN = 32u,     // a captured pipeline no longer fits its data: skip, re-plan
 };
+
+// Kernels of a captured pipeline stop at once when the pipeline has been
+// invalidated earlier in the same run (sizes or capacities changed).
+__device__ __forceinline__ bool replan_pending(const uint32_t* status) {
+  return status != nullptr && (*((volatile const uint32_t*)status) & ST_REPLAN) != 0u;
+}
 
 // Spin bound for decoupled look-back and work queues: about a second at
 // most on a GB300 before the wait is abandoned with ST_TIMEOUT.
@@ -128,6 +135,16 @@ __device__ __forceinline__ int tile_of_key(const Tile* tiles, int ntiles, uint32
   while (a < b) {
     int m = (a + b + 1) >> 1;
     if (tiles[m].key_base <= key) a = m; else b = m - 1;
+  }
+  return a;
+}
+
+// Tile owning a point id of the concatenated input (binary search over pt_base).
+__device__ __forceinline__ int tile_of_id(const Tile* tiles, int ntiles, uint32_t id) {
+  int a = 0, b = ntiles - 1;
+  while (a < b) {
+    int m = (a + b + 1) >> 1;
+    if (tiles[m].pt_base <= id) a = m; else b = m - 1;
   }
   return a;
 }

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
        e += gridDim.x * (blockDim.x / 32)) {
     const uint32_t qid = slow_list[e];
     const double* c = q64 + 3 * (size_t)qid;
-    const Tile& T = ix.tiles[0];
+    const Tile& T = ix.tiles[(qs.all_points && ix.ntiles > 1) ? tile_of_id(ix.tiles, ix.ntiles, qid) : 0];
     // the query's voxel (clamped), from binary64
     int cc[3] = {0, 0, 0};
     for (int a = 0; a < ix.dim; ++a) {
@@ -480,7 +480,8 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
                    cudaStream_t st) {
   if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
-  if (ix->ntiles != 1) return fail(CG_ERR_UNIMPLEMENTED, "k-NN on a batched index");
+  if (!all_points && ix->ntiles != 1)
+    return fail(CG_ERR_UNIMPLEMENTED, "external k-NN queries on a batched index (every point queries its own tile)");
   if (!all_points) {
     cg_status s = prepare_queries(ix, q, nq, st);
     if (s != CG_OK) return s;

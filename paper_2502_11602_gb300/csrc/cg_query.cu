@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
                                                     const int64_t* __restrict__ offsets,
                                                     int32_t* __restrict__ out, HeavyOut heavy,
                                                     unsigned* work_ctr, uint32_t* status) {
+  if (replan_pending(status)) return;
   using R = typename RecT<PREC>::T;
   constexpr int KMAX = RecT<PREC>::KMAX;
   extern __shared__ __align__(32) unsigned char smem[];
@@ -387,7 +388,8 @@ __global__ void __launch_bounds__(512) row_sort_kernel(const uint32_t* __restric
                                                        const uint32_t* __restrict__ count_p,
                                                        uint32_t cap, const int64_t* __restrict__ off,
                                                        int32_t* __restrict__ out,
-                                                       int32_t* __restrict__ scratch) {
+                                                       int32_t* __restrict__ scratch, const uint32_t* status) {
+  if (replan_pending(status)) return;
   extern __shared__ int32_t sbuf[];  // kSmemSortCap entries
   uint32_t cnt = min(*count_p, cap);
   for (uint32_t e = blockIdx.x; e < cnt; e += gridDim.x) {
@@ -755,7 +757,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
         return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
       Lbig.qs.blk_list = R.big_list;
       e = launch_radius_plan(ix->precision, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
-                             R.ctrs + 12, st);
+                             R.ctrs + 12, ix->status, st);
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, ix->status, st);
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, ix->status, st);
       uint32_t tots[3] = {0, 0, 0};
@@ -785,10 +787,10 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
       if (e == cudaSuccess) {
         if (ix->precision == CG_FP32_OFFSET)
           e = launch_radius_fill3(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, R.meta, offsets, out,
-                                  R.ctrs + 16, st);
+                                  R.ctrs + 16, ix->status, st);
         else
           e = launch_radius_fill2(ix->precision, L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets,
-                                  out, R.ctrs + 16, st);
+                                  out, R.ctrs + 16, ix->status, st);
       }
       if (e == cudaSuccess && R.big_n > 0)
         e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, ix->status, grid,
@@ -838,7 +840,8 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     }
     const size_t smem = 4 * kSmemSortCap;
     row_sort_kernel<<<grid_for(R.heavy_count, 1, 152 * 4), 512, smem, st>>>(
-        R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch); note_launch();
+        R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch,
+        ix->status); note_launch();
     e = cudaGetLastError();
     if (scratch) dev_free(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "row sort");

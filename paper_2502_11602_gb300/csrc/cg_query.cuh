@@ -118,7 +118,7 @@ struct BlockPlan {
 // Fast radius kernels (cg_radius2.cu).
 cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, cudaStream_t st);
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st);
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
                                  const Thresholds* thr, const BlockPlan* plans, const uint32_t* moff,
                                  const uint32_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
@@ -126,7 +126,7 @@ cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const 
 cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
-                                cudaStream_t st);
+                                const uint32_t* status, cudaStream_t st);
 
 cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                  const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
@@ -135,7 +135,7 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
 cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
-                                unsigned* work, cudaStream_t st);
+                                unsigned* work, const uint32_t* status, cudaStream_t st);
 
 // Builds (or reuses) the plan of an external query set on ix->plan.
 cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st);

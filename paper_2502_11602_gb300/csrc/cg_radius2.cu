@@ -92,9 +92,11 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
                                                          BlockPlan* __restrict__ plans,
                                                          uint32_t* __restrict__ msize,
                                                          uint32_t* __restrict__ isize,
-                                                         uint32_t* __restrict__ big_list, uint32_t* big_n) {
+                                                         uint32_t* __restrict__ big_list, uint32_t* big_n,
+                                                         const uint32_t* status) {
   using R = typename R2<PREC>::T;
   constexpr int KW = R2<PREC>::KW;
+  if (replan_pending(status)) return;
   const Thresholds thr = *thr_p;
   const unsigned lane = threadIdx.x & 31u;
   const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32) : reinterpret_cast<const R*>(ix.pts64s);
@@ -328,6 +330,7 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
                                                            uint32_t* __restrict__ masks,
                                                            uint32_t* __restrict__ ids, unsigned* work,
                                                            uint32_t* status, int passes) {
+  if (replan_pending(status)) return;
   using R = typename R2<PREC>::T;
   using SM = CountSmem<PREC>;
   constexpr int EPL = SM::KW / CT;
@@ -560,6 +563,7 @@ __global__ void __launch_bounds__(TPB) radius_count3_kernel(IndexView ix, QueryS
                                                            uint32_t* __restrict__ ids,
                                                            uint32_t* __restrict__ meta, unsigned* work,
                                                            uint32_t* status, uint32_t cls) {
+  if (replan_pending(status)) return;
   using SM = Count3Smem<KWc>;
   constexpr int NW = TPB / 32;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -979,7 +983,9 @@ __global__ void __launch_bounds__(W4 * 32) radius_count4_kernel(IndexView ix, Qu
                                                                 uint32_t* __restrict__ counts,
                                                                 uint32_t* __restrict__ masks,
                                                                 uint32_t* __restrict__ ids,
-                                                                uint32_t* __restrict__ meta, unsigned* work) {
+                                                                uint32_t* __restrict__ meta, unsigned* work,
+                                                                const uint32_t* status) {
+  if (replan_pending(status)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   Count4Warp& S = reinterpret_cast<Count4Warp*>(smem)[threadIdx.x >> 5];
   const unsigned lane = threadIdx.x & 31u;
@@ -1164,7 +1170,9 @@ __global__ void __launch_bounds__(TPB) radius_fill3_kernel(IndexView ix, QuerySe
                                                           const uint32_t* __restrict__ ids,
                                                           const uint32_t* __restrict__ meta,
                                                           const int64_t* __restrict__ offsets,
-                                                          int32_t* __restrict__ out, unsigned* work) {
+                                                          int32_t* __restrict__ out, unsigned* work,
+                                                          const uint32_t* status) {
+  if (replan_pending(status)) return;
   constexpr int KW = R2<1>::KW;
   __shared__ uint32_t sids[KW];
   __shared__ uint16_t idxg[KW];
@@ -1293,7 +1301,9 @@ __global__ void __launch_bounds__(CT) radius_fill2_kernel(IndexView ix, QuerySet
                                                           const uint32_t* __restrict__ masks,
                                                           const uint32_t* __restrict__ ids,
                                                           const int64_t* __restrict__ offsets,
-                                                          int32_t* __restrict__ out, unsigned* work) {
+                                                          int32_t* __restrict__ out, unsigned* work,
+                                                          const uint32_t* status) {
+  if (replan_pending(status)) return;
   using R = typename R2<PREC>::T;
   constexpr int KW = R2<PREC>::KW;
   __shared__ uint32_t sids[KW];
@@ -1390,12 +1400,12 @@ int resident_grid(F kern, int threads, size_t smem) {
 
 cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, cudaStream_t st) {
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st) {
   const int grid = (int)std::min<int64_t>((qs.nblocks + 3) / 4 + 1, (int64_t)sm_count() * 16);
   if (prec == CG_FP32_OFFSET)
-    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n);
+    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status);
   else
-    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n);
+    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status);
   note_launch();
   return cudaGetLastError();
 }
@@ -1429,13 +1439,13 @@ cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const 
 cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
-                                cudaStream_t st) {
+                                const uint32_t* status, cudaStream_t st) {
   if (prec == CG_FP32_OFFSET) {
     auto kfn = radius_fill2_kernel<1>;
-    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work);
+    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
   } else {
     auto kfn = radius_fill2_kernel<0>;
-    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work);
+    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
   }
   note_launch();
   return cudaGetLastError();
@@ -1461,14 +1471,14 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
     auto k4 = radius_count4_kernel<CG_SPHERE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
     k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                  ids, meta, work);
+                                                                  ids, meta, work, status);
     note_launch();
     CG_C3(CG_SPHERE, 256, 2048, 1u, work + 1);
   } else {
     auto k4 = radius_count4_kernel<CG_CUBE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
     k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                  ids, meta, work);
+                                                                  ids, meta, work, status);
     note_launch();
     CG_C3(CG_CUBE, 256, 2048, 1u, work + 1);
   }
@@ -1479,9 +1489,10 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
 cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
-                                unsigned* work, cudaStream_t st) {
+                                unsigned* work, const uint32_t* status, cudaStream_t st) {
   auto kfn = radius_fill3_kernel<256>;
-  kfn<<<resident_grid(kfn, 256, 0), 256, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, meta, offsets, out, work);
+  kfn<<<resident_grid(kfn, 256, 0), 256, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, meta, offsets, out, work,
+                                                   status);
   note_launch();
   return cudaGetLastError();
 }
