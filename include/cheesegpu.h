@@ -115,8 +115,9 @@ cg_status cg_build(const double* xyz_dev, int64_t n, double cell_xy, double cell
 /*
  * cg_build_batched -- index T independent tiles in one index (each tile its
  * own bounding box, origin, grid and cell size; voxel keys of different
- * tiles never collide).  Queries against a batched index are per tile: see
- * cg_query_all_points_batched.
+ * tiles never collide).  Queries against a batched index are per tile: every
+ * point queries its own tile (cg_all_points_count / _fill / _knn); external
+ * queries need a single-tile index.
  *  xyz_dev       device float64 [N][3], tiles concatenated.
  *  tile_offsets  HOST int64 [T+1], tile t owns points [off[t], off[t+1]).
  *  T             number of tiles, >= 1; every tile non-empty.
@@ -248,6 +249,80 @@ cg_status cg_all_points_knn(cg_index_t index, int32_t k, int32_t* idx_dev, doubl
  */
 cg_status cg_offsets_scan_noalloc(const uint32_t* counts_dev, int64_t n, int64_t* offsets_dev,
                                   void* stream);
+
+/*
+ * Captured batched pipeline.  The whole hot path over a batch of tiles
+ * (Section 3 build: bounding boxes, voxel keys, stable radix sort, gather,
+ * runs, dense cell table; Algorithm 1 for every indexed point: count, scan,
+ * fill with rows ascending by id; Algorithm 2's exact k-NN result for every
+ * indexed point), recorded once as a CUDA graph and replayed.  A replay
+ * re-reads the coordinates at xyz_dev (the buffer given at creation: same
+ * tile sizes, new values), recomputes every tile's box, origin and binary32
+ * error bounds on the device and writes the pipeline's own outputs, with no
+ * host synchronisation, allocation or per-kernel launch.
+ *
+ * Sizes that depend on the data (non-empty voxels, candidate masks, output
+ * length, long-row scratch) are checked on the device against capacities
+ * fixed at creation (measured sizes x headroom).  Data that outgrows one of
+ * them, or that changes a tile's grid dimensions, raises an internal re-plan
+ * flag: the rest of that replay writes nothing, and the next cg_pipeline_run
+ * with total_host != NULL plans again from the current coordinates (new
+ * buffers: fetch the output pointers again) and replays.  The flavour is
+ * dense; results are identical to cg_build_batched + cg_all_points_* on the
+ * same coordinates.
+ */
+typedef struct cg_pipeline* cg_pipeline_t;
+
+typedef struct {
+  double radius;   /* > 0, finite                                        */
+  int32_t kernel;  /* CG_SPHERE or CG_CUBE                               */
+  int32_t k;       /* 0: no k-NN stage, else 1..64                       */
+  double headroom; /* capacity factor for data-dependent buffers:
+                      0 (default 1.25) or in [1, 16]                      */
+} cg_pipeline_opts_t;
+
+/*
+ *  xyz_dev      device float64 [N][3], tiles concatenated; read by every
+ *               replay (must stay allocated until cg_pipeline_free).
+ *  tile_offsets HOST int64 [T+1], as cg_build_batched.  cell_host  HOST [T].
+ *  dim 2 or 3; precision CG_FP64 or CG_FP32_OFFSET.
+ * Plans on the current coordinates (one eager build and count pass), then
+ * records the graph; synchronises `stream`.  Errors as cg_build_batched,
+ * plus CG_ERR_INVALID for bad options and CG_ERR_CUDA if the capture fails.
+ */
+cg_status cg_pipeline_create(const double* xyz_dev, const int64_t* tile_offsets, int32_t T,
+                             const double* cell_host, int dim, cg_precision precision,
+                             const cg_pipeline_opts_t* opts, void* stream, cg_pipeline_t* out);
+
+/* Replays the graph on `stream`.  With total_host == NULL the call is
+   asynchronous and reports nothing about this replay.  Otherwise it
+   synchronises, handles a pending re-plan (see above), returns any device
+   error (as cg_index_status) and writes the number of radius neighbours. */
+cg_status cg_pipeline_run(cg_pipeline_t p, void* stream, int64_t* total_host);
+
+/* The pipeline-owned device outputs of the last replay (valid until the next
+   re-plan or cg_pipeline_free): offsets int64 [N+1] and indices int32
+   [offsets[N]] (CSR, original point ids, rows ascending); knn_idx int32
+   [N][k] and knn_d2 float64 [N][k] (NULL when k = 0), ordered by (d2, id). */
+cg_status cg_pipeline_outputs(cg_pipeline_t p, int64_t** offsets, int32_t** indices,
+                              int32_t** knn_idx, double** knn_d2);
+
+typedef struct {
+  int64_t n;
+  int32_t ntiles, k;
+  int32_t graph_kernels;     /* kernel nodes launched by one replay        */
+  int32_t graph_nodes;       /* all nodes (kernels, memsets, copies)       */
+  int64_t replans;           /* re-plans since creation                    */
+  int64_t capacity_indices;  /* room for radius neighbours                 */
+  int64_t capacity_voxels;   /* room for non-empty voxels                  */
+  int64_t ncell;             /* voxels of all tiles' grids                 */
+  int64_t device_bytes;      /* device memory held by the pipeline         */
+} cg_pipeline_info_t;
+
+cg_status cg_pipeline_info(cg_pipeline_t p, cg_pipeline_info_t* info);
+
+/* Waits for the last replay, then releases everything the pipeline holds. */
+cg_status cg_pipeline_free(cg_pipeline_t p);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4:
 EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count", "cg_build", "cg_build_batched",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
-           "cg_all_points_knn", "cg_offsets_scan_noalloc"]
+           "cg_all_points_knn", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
+           "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free"]
 
 
 class CheeseError(RuntimeError):
@@ -47,6 +48,19 @@ class IndexInfo(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("nc", ctypes.c_int64 * 3),
                 ("cell", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
                 ("enc_err", ctypes.c_double)]
+
+
+class PipelineOpts(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_double), ("kernel", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("headroom", ctypes.c_double)]
+
+
+class PipelineInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("ntiles", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("graph_kernels", ctypes.c_int32), ("graph_nodes", ctypes.c_int32),
+                ("replans", ctypes.c_int64), ("capacity_indices", ctypes.c_int64),
+                ("capacity_voxels", ctypes.c_int64), ("ncell", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -87,6 +101,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_knn": [P, P, I64, I32, P, P, P],
             "cg_all_points_knn": [P, I32, P, P, P],
             "cg_offsets_scan_noalloc": [P, I64, P, P],
+            "cg_pipeline_create": [P, P, I32, P, I, I, P, P, P],
+            "cg_pipeline_run": [P, P, P],
+            "cg_pipeline_outputs": [P, P, P, P, P],
+            "cg_pipeline_info": [P, P],
+            "cg_pipeline_free": [P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -205,7 +224,107 @@ def cg_all_points_knn(h, k, idx, d2=None, stream=None):
     _check(load().cg_all_points_knn(h, int(k), _ptr(idx), _ptr(d2), _stream(stream)))
 
 
+def cg_pipeline_create(xyz: torch.Tensor, tile_offsets, cells, dim: int, precision: int, radius: float,
+                       kernel: int = SPHERE, k: int = 0, headroom: float = 0.0, stream=None) -> int:
+    import numpy as np
+    if xyz.dtype != torch.float64 or xyz.dim() != 2 or xyz.shape[1] != 3 or not xyz.is_contiguous():
+        raise ValueError("points must be a contiguous float64 tensor of shape (n, 3)")
+    toff = np.ascontiguousarray(tile_offsets, dtype=np.int64)
+    cel = np.ascontiguousarray(cells, dtype=np.float64)
+    opts = PipelineOpts(float(radius), int(kernel), int(k), float(headroom))
+    h = ctypes.c_void_p()
+    _check(load().cg_pipeline_create(_ptr(xyz), toff.ctypes.data, len(toff) - 1, cel.ctypes.data, dim, precision,
+                                     ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def cg_pipeline_run(h: int, want_total: bool = True, stream=None):
+    tot = ctypes.c_int64(0)
+    _check(load().cg_pipeline_run(h, _stream(stream), ctypes.byref(tot) if want_total else None))
+    return tot.value if want_total else None
+
+
+def cg_pipeline_outputs(h: int) -> tuple[int, int, int, int]:
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    _check(load().cg_pipeline_outputs(h, *[ctypes.byref(p) for p in ptrs]))
+    return tuple(p.value or 0 for p in ptrs)
+
+
+def cg_pipeline_info(h: int) -> dict:
+    info = PipelineInfo()
+    _check(load().cg_pipeline_info(h, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in PipelineInfo._fields_}
+
+
+def cg_pipeline_free(h: int):
+    _check(load().cg_pipeline_free(h))
+
+
+class _DeviceArray:
+    """A zero-copy view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+def _view(ptr: int, shape, typestr: str, device) -> torch.Tensor:
+    if ptr == 0 or 0 in tuple(shape):
+        dt = {"<i8": torch.int64, "<i4": torch.int32, "<f8": torch.float64}[typestr]
+        return torch.empty(shape, dtype=dt, device=device)
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=device)
+
+
 # ------------------------------------------------------------- convenience
+
+
+class Pipeline:
+    """Graph-captured batched pipeline (build + all-points radius search +
+    all-points k-NN) over the tiles of ``xyz``; ``run()`` replays it on the
+    current contents of ``xyz`` (same tile sizes)."""
+
+    def __init__(self, xyz: torch.Tensor, tile_offsets, cells, radius: float, kernel: int = SPHERE, k: int = 0,
+                 dim: int = 2, precision: int = FP32_OFFSET, headroom: float = 0.0, stream=None):
+        self.xyz = xyz  # the pipeline reads this buffer on every replay
+        self.n = xyz.shape[0]
+        self.k = k
+        self.device = xyz.device
+        self.total = None
+        self.h = cg_pipeline_create(xyz, tile_offsets, cells, dim, precision, radius, kernel, k, headroom, stream)
+
+    def run(self, stream=None, sync: bool = True):
+        t = cg_pipeline_run(self.h, sync, stream)
+        if sync:
+            self.total = t
+        return t
+
+    def outputs(self) -> dict:
+        """Views of the last replay's outputs (pipeline-owned memory: copy
+        what must outlive the next run).  Needs a synchronising run."""
+        if self.total is None:
+            raise RuntimeError("outputs need a run with sync=True")
+        off, ind, kidx, kd2 = cg_pipeline_outputs(self.h)
+        out = {"offsets": _view(off, (self.n + 1,), "<i8", self.device),
+               "indices": _view(ind, (self.total,), "<i4", self.device)}
+        if self.k > 0:
+            out["knn_idx"] = _view(kidx, (self.n, self.k), "<i4", self.device)
+            out["knn_d2"] = _view(kd2, (self.n, self.k), "<f8", self.device)
+        return out
+
+    def info(self) -> dict:
+        return cg_pipeline_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cg_pipeline_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 
 class Index:

@@ -232,8 +232,11 @@ __global__ void tiles_refresh_kernel(Tile* tiles, int ntiles, const unsigned lon
   if (!same) atomicOr(status, ST_REPLAN);
 }
 
-__global__ void count_check_kernel(const uint32_t* __restrict__ value, uint32_t expected, uint32_t* status) {
-  if (*value != expected) atomicOr(status, ST_REPLAN);
+__global__ void voxel_count_dev_kernel(const uint32_t* __restrict__ ukeys, const uint32_t* __restrict__ ustart,
+                                       const uint32_t* __restrict__ m_dev, uint32_t cap, uint32_t* __restrict__ cnt) {
+  const uint32_t m = min(*m_dev, cap);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+    cnt[ukeys[r]] = ustart[r + 1] - ustart[r];
 }
 
 __global__ void voxel_count_kernel(const uint32_t* __restrict__ ukeys,
@@ -531,7 +534,13 @@ cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st) {
   w.scan_scr = w.bufs.get(scan_scratch_bytes(std::max<int64_t>(n, ix->ncell + 1)), st);
   w.bb = (unsigned long long*)w.bufs.get(8 * 6 * (size_t)ix->ntiles, st);
   w.toff = (int64_t*)w.bufs.get(8 * (size_t)(ix->ntiles + 1), st);
-  if (!w.keys || !w.skeys || !w.flag || !w.rank || !w.cnt || !w.sort_scr || !w.scan_scr || !w.bb || !w.toff)
+  // voxel runs: room for every possible non-empty voxel, so that new data
+  // of the same tile sizes never needs a larger table
+  w.cap_keys = (uint32_t)std::min<int64_t>(n, ix->ncell);
+  w.ukeys = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_keys, st);
+  w.ustart = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_keys + 4, st);
+  if (!w.keys || !w.skeys || !w.flag || !w.rank || !w.cnt || !w.sort_scr || !w.scan_scr || !w.bb || !w.toff ||
+      !w.ukeys || !w.ustart)
     return fail(CG_ERR_OOM, "device allocation failed (pipeline build work)");
   std::vector<int64_t> toff(ix->ntiles + 1);
   for (int t = 0; t < ix->ntiles; ++t) toff[t] = ix->tiles_host[t].pt_base;
@@ -542,7 +551,10 @@ cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st) {
   int bits = 0;
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)ix->ncell) ++bits;
   w.bits = bits;
-  w.nkeys = ix->nkeys;
+  w.nkeys_dev = w.rank + n;
+  // the index now reads its runs from the pipeline's tables
+  ix->ukeys = w.ukeys;
+  ix->ustart = w.ustart;
   return CG_OK;
 }
 
@@ -564,17 +576,19 @@ cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream
   if (e != cudaSuccess) return cuda_fail(e, "replay sort");
   gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->sid, w.skeys, ix->tiles, T, ix->pts32,
                                                              ix->pts64s); note_launch();
-  e = cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "replay copy");
+  if (ix->xyz64 != xyz) {  // a pipeline reads the caller's buffer in place
+    e = cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "replay copy");
+  }
   run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag); note_launch();
   e = exclusive_scan_u32_u32(w.flag, w.rank, n, w.scan_scr, ix->status, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay scan");
   run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag, w.rank, ix->ukeys, ix->ustart,
-                                                               w.nkeys); note_launch();
-  count_check_kernel<<<1, 1, 0, st>>>(w.rank + n, w.nkeys, ix->status); note_launch();
+                                                               w.cap_keys); note_launch();
   e = cudaMemsetAsync(w.cnt, 0, 4 * (size_t)ix->ncell, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay memset");
-  voxel_count_kernel<<<grid_for(w.nkeys, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, w.nkeys, w.cnt); note_launch();
+  voxel_count_dev_kernel<<<grid_for(w.cap_keys, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, w.nkeys_dev,
+                                                                              w.cap_keys, w.cnt); note_launch();
   e = exclusive_scan_u32_u32(w.cnt, ix->cstart, ix->ncell, w.scan_scr, ix->status, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay cell starts");
   return CG_OK;

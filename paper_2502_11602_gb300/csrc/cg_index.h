@@ -77,6 +77,30 @@ struct RadiusState {
   uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
   uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr, *meta = nullptr;
   uint32_t big_n = 0;
+  uint32_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
+};
+
+// Workspace of a replayed radius pass: every data-dependent buffer sized
+// once with headroom; kernels flag ST_REPLAN when new data outgrows them.
+struct RadiusWork {
+  DevBufs bufs;
+  uint32_t *counts = nullptr, *heavy_list = nullptr, *heavy_soff = nullptr, *ctrs = nullptr;
+  Thresholds* thr = nullptr;
+  void *scan_scr = nullptr, *plan_scr = nullptr;
+  struct BlockPlan* plans = nullptr;
+  uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
+  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr, *meta = nullptr;
+  int32_t* row_scratch = nullptr;
+  uint32_t cap_nb = 0, cap_m = 0, cap_i = 0;
+  uint64_t cap_scr = 0;
+  int64_t cap_out = 0;
+};
+
+// Workspace of a replayed k-NN pass.
+struct KnnWork {
+  DevBufs bufs;
+  uint32_t *slow = nullptr, *ctrs = nullptr;
+  Thresholds* thr = nullptr;
 };
 
 // Workspace of a replayed (graph-captured) build.
@@ -86,8 +110,10 @@ struct BuildWork {
   void *sort_scr = nullptr, *scan_scr = nullptr;
   unsigned long long* bb = nullptr;
   int64_t* toff = nullptr;
+  uint32_t *ukeys = nullptr, *ustart = nullptr;  // [cap_keys], [cap_keys + 1]
+  const uint32_t* nkeys_dev = nullptr;           // non-empty voxels of the last replay
+  uint32_t cap_keys = 0;
   int bits = 0;
-  uint32_t nkeys = 0;
 };
 
 }  // namespace cg
@@ -150,4 +176,11 @@ namespace cg {
 cg_status check_status(cg_index* ix, cudaStream_t st);
 cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
 cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
+cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,
+                            cudaStream_t st);
+cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, double r, int kernel,
+                        int64_t* offsets, int32_t* out, cudaStream_t st);
+cg_status knn_work_alloc(cg_index* ix, KnnWork& w, cudaStream_t st);
+cg_status knn_replay(cg_index* ix, KnnWork& w, const uint32_t* nkeys_dev, uint32_t cap_nb, int k, int32_t* idx,
+                     double* d2, cudaStream_t st);
 }  // namespace cg

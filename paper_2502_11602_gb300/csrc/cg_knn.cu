@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
                                                      int k, int32_t* __restrict__ out_idx, double* __restrict__ out_d2,
                                                      uint32_t* __restrict__ slow_list, uint32_t* slow_cnt,
                                                      unsigned* work, uint32_t* status) {
+  if (replan_pending(status)) return;  // the slow kernel then finds an empty list
   using R = typename KRec<PREC>::T;
   constexpr int KMAX = KRec<PREC>::KMAX;
   extern __shared__ __align__(32) unsigned char smem[];
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
     if (threadIdx.x == 0) s_blk = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t b = s_blk;
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
     const uint32_t bkey = qs.blk_key[b];
     const int ti = ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey);
@@ -466,12 +467,24 @@ size_t knn_smem() {
 
 // k-NN error terms: pad_[0] = alpha = e_p + e_q (per-axis bound on the
 // binary32 difference error), e_q = the queries' own encode bound.
-__global__ void knn_thr_kernel(Thresholds* out, double e_p, const uint32_t* maxoff_bits) {
-  double m = maxoff_bits ? (double)__uint_as_float(*maxoff_bits) : 0.0;
-  double e_q = maxoff_bits ? ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30 : e_p;
+__device__ void knn_thresholds(Thresholds* out, double e_p, double e_q) {
   Thresholds t = make_thresholds(1.0, e_p, e_q);
   t.pad_[0] = __double2float_ru((e_p + e_q) * (1.0 + 1e-6));
   *out = t;
+}
+
+__global__ void knn_thr_kernel(Thresholds* out, double e_p, const uint32_t* maxoff_bits) {
+  double m = maxoff_bits ? (double)__uint_as_float(*maxoff_bits) : 0.0;
+  double e_q = maxoff_bits ? ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30 : e_p;
+  knn_thresholds(out, e_p, e_q);
+}
+
+// replayed pipelines: the encode bound of the refreshed tiles
+__global__ void knn_thr_tiles_kernel(Thresholds* out, const Tile* __restrict__ tiles, int ntiles) {
+  float e = 0.f;
+  for (int t = threadIdx.x; t < ntiles; t += 32) e = fmaxf(e, tiles[t].enc_err);
+  for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (threadIdx.x == 0) knn_thresholds(out, (double)e, (double)e);
 }
 
 }  // namespace
@@ -543,6 +556,57 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
   e = cudaGetLastError();
   tmp.release(st);
   if (e != cudaSuccess) return cuda_fail(e, "k-NN kernels");
+  return CG_OK;
+}
+
+
+cg_status knn_work_alloc(cg_index* ix, KnnWork& w, cudaStream_t st) {
+  w.slow = (uint32_t*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->n, 1), st);
+  w.ctrs = (uint32_t*)w.bufs.get(256, st);
+  w.thr = (Thresholds*)w.bufs.get(sizeof(Thresholds), st);
+  if (!w.slow || !w.ctrs || !w.thr) return fail(CG_ERR_OOM, "device allocation failed (pipeline k-NN work)");
+  return CG_OK;
+}
+
+// All-points k-NN with the block count read on the device (no host
+// synchronisation or allocation).
+cg_status knn_replay(cg_index* ix, KnnWork& w, const uint32_t* nkeys_dev, uint32_t cap_nb, int k, int32_t* idx,
+                     double* d2, cudaStream_t st) {
+  if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
+  cudaError_t e = cudaMemsetAsync(w.ctrs, 0, 256, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay memset");
+  knn_thr_tiles_kernel<<<1, 32, 0, st>>>(w.thr, ix->tiles, ix->ntiles); note_launch();
+  QuerySet qs;
+  qs.all_points = 1;
+  qs.nq = (uint32_t)ix->n;
+  qs.nblocks = cap_nb;
+  qs.nblocks_dev = nkeys_dev;
+  qs.blk_beg = ix->ustart;
+  qs.blk_key = ix->ukeys;
+  qs.qrec = ix->pts32;
+  qs.qrec64 = ix->pts64s;
+  qs.q64 = ix->xyz64;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const IndexView iv = ix->view();
+  if (ix->precision == CG_FP32_OFFSET) {
+    const size_t smem = knn_smem<1>();
+    cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
+    knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, w.thr, k, idx, d2, w.slow, w.ctrs, w.ctrs + 4,
+                                                     ix->status); note_launch();
+    knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, w.slow, w.ctrs, idx, d2); note_launch();
+  } else {
+    const size_t smem = knn_smem<0>();
+    cudaFuncSetAttribute(knn_fast_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
+    knn_fast_kernel<0><<<sms * per, KT, smem, st>>>(iv, qs, w.thr, k, idx, d2, w.slow, w.ctrs, w.ctrs + 4,
+                                                     ix->status); note_launch();
+    knn_slow_kernel<0><<<sms * 8, 128, 0, st>>>(iv, qs, k, w.slow, w.ctrs, idx, d2); note_launch();
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "replay k-NN kernels");
   return CG_OK;
 }
 

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
       if (wi >= *qs.blk_list_n) break;
       b = qs.blk_list[wi];
     } else {
-      if (wi >= qs.nblocks) break;
+      if (wi >= qs_nblocks(qs)) break;
       b = wi;
     }
     const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
@@ -533,6 +533,26 @@ size_t radius_smem() {
   return sizeof(R) * (RecT<PREC>::KMAX + QB) + sizeof(long long) * QB + 4 * QB + 4 * (2 * MAX_SPANS + 1);
 }
 
+// all-points thresholds of a replayed pass, from the refreshed tiles
+__global__ void replay_thresholds_kernel(Thresholds* out, const Tile* __restrict__ tiles, int ntiles, double r) {
+  float e = 0.f;
+  for (int t = threadIdx.x; t < ntiles; t += 32) e = fmaxf(e, tiles[t].enc_err);
+  for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (threadIdx.x == 0) *out = make_thresholds(r, (double)e, (double)e);
+}
+
+// capacity checks of a replayed pass: new data that outgrows a buffer
+// stops the rest of the run (every later kernel tests ST_REPLAN first)
+__global__ void replay_check_plan_kernel(const uint32_t* __restrict__ moff_end, uint32_t cap_m,
+                                         const uint32_t* __restrict__ idoff_end, uint32_t cap_i, uint32_t* status) {
+  if (*moff_end > cap_m || *idoff_end > cap_i) atomicOr(status, ST_REPLAN);
+}
+__global__ void replay_check_out_kernel(const int64_t* __restrict__ total, int64_t cap_out,
+                                        const unsigned long long* __restrict__ scratch_total, uint64_t cap_scr,
+                                        uint32_t* status) {
+  if (*total > cap_out || *scratch_total > cap_scr) atomicOr(status, ST_REPLAN);
+}
+
 }  // namespace
 
 // -------------------------------------------------------------- host side
@@ -770,6 +790,8 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
       R.ids = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[1], 1), st);
       if (!R.masks || !R.ids) return fail(CG_ERR_OOM, "device allocation failed (radius masks)");
       R.big_n = tots[2];
+      R.mtot = tots[0];
+      R.itot = tots[1];
       if (ix->precision == CG_FP32_OFFSET) {
         R.meta = (uint32_t*)R.bufs.get(16 * (size_t)nb, st);
         if (!R.meta) return fail(CG_ERR_OOM, "device allocation failed (radius meta)");
@@ -846,6 +868,112 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     if (scratch) dev_free(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "row sort");
   }
+  return CG_OK;
+}
+
+
+// ------------------------------------------------- replayed (graph) pass
+
+cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,
+                            cudaStream_t st) {
+  const RadiusState& R = ix->radius;
+  const int64_t n = std::max<int64_t>(ix->n, 1);
+  auto grow = [&](double v, double slack) { return v * headroom + slack; };
+  w.cap_nb = std::max<uint32_t>(cap_nb, 1);
+  w.cap_m = (uint32_t)std::min(grow(R.mtot, 65536.0), 4.0e9);
+  w.cap_i = (uint32_t)std::min(grow(R.itot, 65536.0), 4.0e9);
+  w.cap_scr = (uint64_t)grow((double)R.heavy_scratch, 1 << 20);
+  w.cap_out = (int64_t)grow((double)total, 1 << 20);
+  w.counts = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.heavy_list = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.heavy_soff = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
+  w.ctrs = (uint32_t*)w.bufs.get(256, st);
+  w.thr = (Thresholds*)w.bufs.get(sizeof(Thresholds), st);
+  w.scan_scr = w.bufs.get(scan_scratch_bytes(n), st);
+  w.plan_scr = w.bufs.get(scan_scratch_bytes(w.cap_nb), st);
+  w.plans = (BlockPlan*)w.bufs.get(sizeof(BlockPlan) * (size_t)w.cap_nb, st);
+  w.msize = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
+  w.isize = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
+  w.moff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
+  w.idoff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
+  w.big_list = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_nb, st);
+  w.meta = (uint32_t*)w.bufs.get(16 * (size_t)w.cap_nb, st);
+  w.masks = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_m, st);
+  w.ids = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_i, st);
+  w.row_scratch = (int32_t*)w.bufs.get(4 * (size_t)w.cap_scr, st);
+  if (!w.counts || !w.heavy_list || !w.heavy_soff || !w.ctrs || !w.thr || !w.scan_scr || !w.plan_scr || !w.plans ||
+      !w.msize || !w.isize || !w.moff || !w.idoff || !w.big_list || !w.meta || !w.masks || !w.ids || !w.row_scratch)
+    return fail(CG_ERR_OOM, "device allocation failed (pipeline radius work)");
+  return CG_OK;
+}
+
+// The all-points radius pass (count, scan, fill, row sort) with no host
+// synchronisation or allocation: sizes come from the device (block count,
+// totals), checked against the capacities of the work buffers.
+cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, double r, int kernel,
+                        int64_t* offsets, int32_t* out, cudaStream_t st) {
+  const int64_t n = ix->n;
+  cudaError_t e = cudaMemsetAsync(w.ctrs, 0, 256, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay memset");
+  replay_thresholds_kernel<<<1, 32, 0, st>>>(w.thr, ix->tiles, ix->ntiles, r); note_launch();
+  RadiusLaunch L;
+  L.iv = ix->view();
+  L.thr = w.thr;
+  L.qs.all_points = 1;
+  L.qs.nq = (uint32_t)n;
+  L.qs.nblocks = w.cap_nb;
+  L.qs.nblocks_dev = nkeys_dev;
+  L.qs.blk_beg = ix->ustart;
+  L.qs.blk_key = ix->ukeys;
+  L.qs.qrec = ix->pts32;
+  L.qs.qrec64 = ix->pts64s;
+  L.qs.q64 = ix->xyz64;
+  RadiusLaunch Lbig = L;
+  Lbig.qs.blk_list = w.big_list;
+  Lbig.qs.blk_list_n = w.ctrs + 12;
+  HeavyOut H;
+  H.list = w.heavy_list;
+  H.scratch_off = w.heavy_soff;
+  H.count = w.ctrs + 0;
+  H.max_len = w.ctrs + 1;
+  H.scratch_total = (unsigned long long*)(w.ctrs + 2);
+  H.cap = (uint32_t)std::max<int64_t>(n, 1);
+  const int grid = radius_grid(ix->precision);
+  const uint32_t nb = w.cap_nb;
+  e = launch_radius_plan(ix->precision, L.iv, L.qs, w.thr, w.plans, w.msize, w.isize, w.big_list, w.ctrs + 12,
+                         ix->status, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.msize, w.moff, nb, w.plan_scr, ix->status, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.isize, w.idoff, nb, w.plan_scr, ix->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay plan");
+  replay_check_plan_kernel<<<1, 1, 0, st>>>(w.moff + nb, w.cap_m, w.idoff + nb, w.cap_i, ix->status); note_launch();
+  if (ix->precision == CG_FP32_OFFSET)
+    e = launch_radius_count3(kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks, w.ids, w.meta,
+                             w.ctrs + 14, ix->status, st);
+  else
+    e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks,
+                             w.ids, w.ctrs + 14, ix->status, st);
+  // groups too large for the fast kernels: the list length is read on the
+  // device, an empty list costs one pass over the grid
+  if (e == cudaSuccess)
+    e = dispatch_radius<false>(ix->precision, kernel, Lbig, w.counts, nullptr, nullptr, H, w.ctrs + 6, ix->status,
+                               grid, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_i64(w.counts, offsets, n, w.scan_scr, ix->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay count");
+  replay_check_out_kernel<<<1, 1, 0, st>>>(offsets + n, w.cap_out, H.scratch_total, w.cap_scr, ix->status); note_launch();
+  if (ix->precision == CG_FP32_OFFSET)
+    e = launch_radius_fill3(L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, w.meta, offsets, out, w.ctrs + 16,
+                            ix->status, st);
+  else
+    e = launch_radius_fill2(ix->precision, L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out,
+                            w.ctrs + 16, ix->status, st);
+  if (e == cudaSuccess)
+    e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, w.ctrs + 8, ix->status, grid,
+                              st);
+  if (e != cudaSuccess) return cuda_fail(e, "replay fill");
+  row_sort_kernel<<<152 * 4, 512, 4 * kSmemSortCap, st>>>(w.heavy_list, w.heavy_soff, w.ctrs + 0, H.cap, offsets, out,
+                                                         w.row_scratch, ix->status); note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "replay row sort");
   return CG_OK;
 }
 

@@ -101,7 +101,14 @@ struct QuerySet {
   const double* q64;           // [nq][3] original order, exact coordinates
   const uint32_t* blk_list = nullptr;    // optional subset of blocks to process
   const uint32_t* blk_list_n = nullptr;  // its length (device)
+  // replayed pipelines: the true block count lives on the device and
+  // nblocks is only its capacity
+  const uint32_t* nblocks_dev = nullptr;
 };
+
+__device__ __forceinline__ uint32_t qs_nblocks(const QuerySet& qs) {
+  return qs.nblocks_dev ? min(*qs.nblocks_dev, qs.nblocks) : qs.nblocks;
+}
 
 // Per voxel group: what the fast radius kernels need (see cg_radius2.cu).
 constexpr int kPlanSpans = 32;  // non-empty voxel runs per group

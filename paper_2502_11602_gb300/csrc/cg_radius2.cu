@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
                                              : (PREC == 1 ? reinterpret_cast<const R*>(qs.qrec)
                                                           : reinterpret_cast<const R*>(qs.qrec64));
   const uint32_t nwarps = gridDim.x * (PT / 32);
-  for (uint32_t b = blockIdx.x * (PT / 32) + (threadIdx.x >> 5); b < qs.nblocks; b += nwarps) {
+  for (uint32_t b = blockIdx.x * (PT / 32) + (threadIdx.x >> 5); b < qs_nblocks(qs); b += nwarps) {
     const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1], nq = qb1 - qb0;
     const uint32_t bkey = qs.blk_key[b];
     const Tile& T = ix.tiles[ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey)];
@@ -180,6 +180,13 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
       if (big) big_list[atomicAdd(big_n, 1u)] = b;
     }
   }
+  // replayed pipelines scan the whole capacity: groups past the true count
+  // contribute nothing
+  if (qs.nblocks_dev != nullptr)
+    for (uint32_t b = qs_nblocks(qs) + blockIdx.x * PT + threadIdx.x; b < qs.nblocks; b += gridDim.x * PT) {
+      msize[b] = 0u;
+      isize[b] = 0u;
+    }
 }
 
 // ------------------------------------------------------------------ count
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
     if (threadIdx.x == 0) s_b = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t b = s_b;
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     if (threadIdx.x < 6) s_hdr[threadIdx.x] = reinterpret_cast<const uint32_t*>(plans + b)[threadIdx.x];
     if (threadIdx.x < kPlanSpans) {
       s_start[threadIdx.x] = plans[b].start[threadIdx.x];
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(TPB) radius_count3_kernel(IndexView ix, QueryS
     if (threadIdx.x == 0) s_b = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t b = s_b;
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     if (threadIdx.x < 6) s_hdr[threadIdx.x] = reinterpret_cast<const uint32_t*>(plans + b)[threadIdx.x];
     if (threadIdx.x < kPlanSpans) {
       s_start[threadIdx.x] = plans[b].start[threadIdx.x];
@@ -1000,7 +1007,7 @@ __global__ void __launch_bounds__(W4 * 32) radius_count4_kernel(IndexView ix, Qu
     uint32_t b = 0;
     if (lane == 0) b = atomicAdd(work, 1u);
     b = __shfl_sync(0xffffffffu, b, 0);
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     const uint32_t* hp = reinterpret_cast<const uint32_t*>(plans + b);
     const uint32_t q0 = __ldg(hp), nq = __ldg(hp + 1), K = __ldg(hp + 2);
     const uint32_t nsp = __ldg(hp + 3) & 0xffffu, heavy = __ldg(hp + 4), cls = __ldg(hp + 5);
@@ -1190,7 +1197,7 @@ __global__ void __launch_bounds__(TPB) radius_fill3_kernel(IndexView ix, QuerySe
     if (threadIdx.x == 0) s_b = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t b = s_b;
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     if (threadIdx.x < 6) s_hdr[threadIdx.x] = reinterpret_cast<const uint32_t*>(plans + b)[threadIdx.x];
     if (threadIdx.x < 3) s_meta[threadIdx.x] = meta[4 * b + threadIdx.x];
     __syncthreads();
@@ -1321,7 +1328,7 @@ __global__ void __launch_bounds__(CT) radius_fill2_kernel(IndexView ix, QuerySet
     if (threadIdx.x == 0) s_b = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t b = s_b;
-    if (b >= qs.nblocks) break;
+    if (b >= qs_nblocks(qs)) break;
     if (threadIdx.x < 6) s_hdr[threadIdx.x] = reinterpret_cast<const uint32_t*>(plans + b)[threadIdx.x];
     __syncthreads();
     const uint32_t q0 = s_hdr[0], nq = s_hdr[1], K = s_hdr[2];
