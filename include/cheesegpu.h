@@ -324,6 +324,99 @@ cg_status cg_pipeline_info(cg_pipeline_t p, cg_pipeline_info_t* info);
 /* Waits for the last replay, then releases everything the pipeline holds. */
 cg_status cg_pipeline_free(cg_pipeline_t p);
 
+/*
+ * Serving loop: continuous batching of query requests against
+ * device-resident indexes (built with cg_build, single tile).  `slots`
+ * worker threads each own a CUDA stream and a private query context, so up
+ * to `slots` requests run at once and their kernels overlap on the GPU.
+ * Admission is first come, first served: the oldest queued request starts
+ * as soon as a slot is free and its memory fits the budget.  A radius
+ * request first reserves its offsets (8 (nq+1) B) and an estimate of the
+ * pass's work; after its count pass it reserves the measured CSR output
+ * (total x 4 B) and work, waiting until other requests free memory.  If
+ * every running request waits for memory, the last admitted one steps back
+ * to the head of the queue (its count is redone when its measured size
+ * fits).  A request that cannot fit the budget even alone completes with
+ * CG_ERR_OOM.  A request's outputs belong to the server and count against
+ * the budget until cg_server_release.  Results are those of cg_radius_count
+ * + cg_radius_fill / cg_knn on the same inputs, alone or in any mix.
+ * The server's calls are thread-safe.  Indexes and query buffers must stay
+ * valid until their requests complete.  Requests never touch an index's
+ * default query context, so other calls may query the same indexes
+ * meanwhile (from one thread at a time, as always).
+ */
+typedef struct cg_server* cg_server_t;
+
+typedef enum { CG_REQ_RADIUS = 0, CG_REQ_KNN = 1 } cg_request_op;
+
+typedef struct {
+  int32_t slots;          /* concurrent requests, 1..64                      */
+  int64_t memory_budget;  /* bytes for requests' outputs and work; 0: half
+                             of the device's free memory at creation        */
+} cg_server_opts_t;
+
+typedef struct {
+  int32_t index;        /* position in the index list given at creation     */
+  int32_t op;           /* cg_request_op                                    */
+  int32_t kernel;       /* radius: CG_SPHERE or CG_CUBE                     */
+  int32_t k;            /* k-NN: 1..64                                      */
+  double radius;        /* radius: > 0, finite                              */
+  const double* q_dev;  /* device float64 [nq][3] query centres             */
+  int64_t nq;           /* >= 0                                             */
+} cg_request_t;
+
+typedef struct {
+  cg_status status;
+  int64_t nq, total;    /* total: radius neighbours (radius requests)       */
+  int64_t* offsets;     /* radius: device int64 [nq+1]                      */
+  int32_t* indices;     /* radius: device int32 [total], rows ascending     */
+  int32_t* knn_idx;     /* k-NN: device int32 [nq][k]                       */
+  double* knn_d2;       /* k-NN: device float64 [nq][k]                     */
+  double queue_ms;      /* submit -> admission                              */
+  double latency_ms;    /* submit -> result complete on the device          */
+} cg_result_t;
+
+typedef struct {
+  int64_t requests_done, requests_failed, queries_done, queued;
+  int32_t in_flight, max_in_flight;
+  int64_t memory_budget, memory_in_use, memory_peak, preemptions;
+  double p50_ms, p99_ms, max_ms;  /* latency of completed requests (nearest rank) */
+  double queries_per_s;           /* completed queries / (last done - first submit) */
+} cg_server_stats_t;
+
+/* Starts the worker threads on the current device.  CG_ERR_INVALID for bad
+   options or a NULL index. */
+cg_status cg_server_create(const cg_index_t* indexes, int32_t n_indexes, const cg_server_opts_t* opts,
+                           cg_server_t* out);
+
+/* Queues a request (never blocks on the GPU) and returns its id.
+   CG_ERR_INVALID for a bad index position, op, radius, kernel, k or query
+   set; CG_ERR_UNIMPLEMENTED for a batched index. */
+cg_status cg_server_submit(cg_server_t server, const cg_request_t* request, int64_t* id);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for a request.  Returns the
+   request's own status (its result is filled in either way), or
+   CG_ERR_TIMEOUT if it has not finished yet. */
+cg_status cg_server_wait(cg_server_t server, int64_t id, double timeout_s, cg_result_t* result);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for any request to finish
+   and returns its id, each finished request once, in completion order
+   (CG_ERR_TIMEOUT if none).  A finished request's outputs hold budget until
+   it is released, so a consumer that waits for one particular request while
+   keeping others' results can stall admission: drain with this call. */
+cg_status cg_server_wait_any(cg_server_t server, double timeout_s, int64_t* id);
+
+/* Frees a finished request's outputs and returns their memory to the
+   budget; the id becomes unknown. */
+cg_status cg_server_release(cg_server_t server, int64_t id);
+
+cg_status cg_server_stats(cg_server_t server, cg_server_stats_t* stats);
+
+/* Drops queued requests, lets running ones finish, stops the workers and
+   frees every output not yet released.  No other thread may be inside a
+   call on this server. */
+cg_status cg_server_free(cg_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,10 @@ EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
            "cg_all_points_knn", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
-           "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free"]
+           "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free", "cg_server_create", "cg_server_submit",
+           "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free"]
+
+REQ_RADIUS, REQ_KNN = 0, 1
 
 
 class CheeseError(RuntimeError):
@@ -61,6 +64,31 @@ class PipelineInfo(ctypes.Structure):
                 ("replans", ctypes.c_int64), ("capacity_indices", ctypes.c_int64),
                 ("capacity_voxels", ctypes.c_int64), ("ncell", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("memory_budget", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int32), ("op", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("radius", ctypes.c_double), ("q_dev", ctypes.c_void_p),
+                ("nq", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nq", ctypes.c_int64), ("total", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p), ("indices", ctypes.c_void_p), ("knn_idx", ctypes.c_void_p),
+                ("knn_d2", ctypes.c_void_p), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_int64), ("requests_failed", ctypes.c_int64),
+                ("queries_done", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int32),
+                ("max_in_flight", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("memory_in_use", ctypes.c_int64), ("memory_peak", ctypes.c_int64),
+                ("preemptions", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("queries_per_s", ctypes.c_double)]
 
 
 _lib = None
@@ -106,6 +134,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_pipeline_outputs": [P, P, P, P, P],
             "cg_pipeline_info": [P, P],
             "cg_pipeline_free": [P],
+            "cg_server_create": [P, I32, P, P],
+            "cg_server_submit": [P, P, P],
+            "cg_server_wait": [P, I64, D, P],
+            "cg_server_wait_any": [P, D, P],
+            "cg_server_release": [P, I64],
+            "cg_server_stats": [P, P],
+            "cg_server_free": [P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -276,6 +311,110 @@ def _view(ptr: int, shape, typestr: str, device) -> torch.Tensor:
 
 
 # ------------------------------------------------------------- convenience
+
+
+def cg_server_create(index_handles, slots: int = 4, memory_budget: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(index_handles))(*index_handles)
+    opts = ServerOpts(int(slots), int(memory_budget))
+    h = ctypes.c_void_p()
+    _check(load().cg_server_create(arr, len(index_handles), ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def cg_server_submit(h: int, index: int, q: torch.Tensor, op: int, radius: float = 0.0, kernel: int = SPHERE,
+                     k: int = 0) -> int:
+    req = Request(int(index), int(op), int(kernel), int(k), float(radius), _ptr(q) if q.shape[0] else None,
+                  int(q.shape[0]))
+    rid = ctypes.c_int64(0)
+    _check(load().cg_server_submit(h, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def cg_server_wait(h: int, rid: int, timeout_s: float = -1.0) -> Result:
+    res = Result()
+    code = load().cg_server_wait(h, rid, float(timeout_s), ctypes.byref(res))
+    _check(code)
+    return res
+
+
+def cg_server_wait_any(h: int, timeout_s: float = -1.0) -> int:
+    rid = ctypes.c_int64(0)
+    _check(load().cg_server_wait_any(h, float(timeout_s), ctypes.byref(rid)))
+    return rid.value
+
+
+def cg_server_release(h: int, rid: int):
+    _check(load().cg_server_release(h, rid))
+
+
+def cg_server_stats(h: int) -> dict:
+    st = ServerStats()
+    _check(load().cg_server_stats(h, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def cg_server_free(h: int):
+    _check(load().cg_server_free(h))
+
+
+class Server:
+    """Continuous-batching request loop over device-resident ``Index``es."""
+
+    def __init__(self, indexes, slots: int = 4, memory_budget: int = 0):
+        self.indexes = list(indexes)  # kept alive while the server runs
+        self.device = self.indexes[0].device
+        self.h = cg_server_create([ix.h for ix in self.indexes], slots, memory_budget)
+        self._queries = {}
+
+    def submit_radius(self, index: int, q: torch.Tensor, r: float, kernel: int = SPHERE) -> int:
+        q = _points(q)
+        rid = cg_server_submit(self.h, index, q, REQ_RADIUS, radius=r, kernel=kernel)
+        self._queries[rid] = (q, None)
+        return rid
+
+    def submit_knn(self, index: int, q: torch.Tensor, k: int) -> int:
+        q = _points(q)
+        rid = cg_server_submit(self.h, index, q, REQ_KNN, k=k)
+        self._queries[rid] = (q, k)
+        return rid
+
+    def wait(self, rid: int, timeout_s: float = -1.0, copy: bool = True) -> dict:
+        """The request's result (device tensors, copied out of server memory
+        when ``copy``), latency and queueing time in ms."""
+        res = cg_server_wait(self.h, rid, timeout_s)
+        q, k = self._queries[rid]
+        out = {"latency_ms": res.latency_ms, "queue_ms": res.queue_ms, "nq": res.nq}
+        if k is None:
+            off = _view(res.offsets or 0, (res.nq + 1,), "<i8", self.device)
+            ind = _view(res.indices or 0, (res.total,), "<i4", self.device)
+            out["offsets"], out["indices"] = (off.clone(), ind.clone()) if copy else (off, ind)
+        else:
+            idx = _view(res.knn_idx or 0, (res.nq, k), "<i4", self.device)
+            d2 = _view(res.knn_d2 or 0, (res.nq, k), "<f8", self.device)
+            out["idx"], out["d2"] = (idx.clone(), d2.clone()) if copy else (idx, d2)
+        return out
+
+    def wait_any(self, timeout_s: float = -1.0) -> int:
+        """Id of the next finished request (completion order)."""
+        return cg_server_wait_any(self.h, timeout_s)
+
+    def release(self, rid: int):
+        cg_server_release(self.h, rid)
+        self._queries.pop(rid, None)
+
+    def stats(self) -> dict:
+        return cg_server_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cg_server_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Pipeline:

@@ -339,6 +339,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   } while (0)
 
   CG_ALLOC(ix->status, uint32_t, 64, ix->bufs);
+  ix->ctx.status = ix->status;
   ix->scratch_u32 = ix->status + 16;
   CG_CUDA(cudaMemsetAsync(ix->status, 0, 64 * 4, st));
 

@@ -83,13 +83,15 @@ void dev_free(void* p, cudaStream_t st) {
   cudaFreeAsync(p, st);
 }
 
-cg_status check_status(cg_index* ix, cudaStream_t st) {
+cg_status check_status(cg_index* ix, cudaStream_t st) { return check_status_word(ix->status, st); }
+
+cg_status check_status_word(uint32_t* status, cudaStream_t st) {
   uint32_t w = 0;
-  cudaError_t e = cudaMemcpyAsync(&w, ix->status, 4, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(&w, status, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "status readback");
   if (w & (ST_NONFINITE | ST_TIMEOUT | ST_OVERFLOW | ST_INTERNAL)) {
-    cudaMemsetAsync(ix->status, 0, 4, st);
+    cudaMemsetAsync(status, 0, 4, st);
     if (w & ST_NONFINITE) return fail(CG_ERR_INVALID, "non-finite query coordinate");
     if (w & ST_TIMEOUT) return fail(CG_ERR_TIMEOUT, "a bounded device wait gave up");
     if (w & ST_OVERFLOW) return fail(CG_ERR_OVERFLOW, "an internal capacity was exceeded");
@@ -184,8 +186,7 @@ cg_status cg_index_info(cg_index_t ix, cg_index_info_t* info) {
 
 cg_status cg_index_free(cg_index_t ix) {
   if (!ix) return fail(CG_ERR_INVALID, "NULL index");
-  ix->radius.bufs.release(ix->stream);
-  ix->plan.bufs.release(ix->stream);
+  ix->ctx.release(ix->stream);
   ix->bufs.release(ix->stream);
   delete ix;
   return CG_OK;

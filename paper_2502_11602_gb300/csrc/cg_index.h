@@ -80,6 +80,22 @@ struct RadiusState {
   uint32_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
 };
 
+// Mutable state of queries against an index: the external query plan, the
+// radius pass carried from count to fill, and the device status word the
+// kernels report into.  An index has one default context; concurrent users
+// of one index (the serving loop's slots) each bring their own.
+struct QueryCtx {
+  QueryPlan plan;
+  RadiusState radius;
+  uint32_t* status = nullptr;
+  void release(cudaStream_t st) {
+    plan.bufs.release(st);
+    radius.bufs.release(st);
+    plan = QueryPlan();
+    radius = RadiusState();
+  }
+};
+
 // Workspace of a replayed radius pass: every data-dependent buffer sized
 // once with headroom; kernels flag ST_REPLAN when new data outgrows them.
 struct RadiusWork {
@@ -142,8 +158,7 @@ struct cg_index {
   uint32_t* status = nullptr;    // device status word (ST_* bits)
   uint32_t* scratch_u32 = nullptr;  // small device scratch
   double enc_err0 = 0;
-  cg::QueryPlan plan;
-  cg::RadiusState radius;
+  cg::QueryCtx ctx;  // default query context (status = the index's word)
   int max_pts_per_voxel = 0;
 
   cg::IndexView view() const {
@@ -174,6 +189,13 @@ struct cg_index {
 namespace cg {
 // Reads and clears the device status word (synchronises the stream).
 cg_status check_status(cg_index* ix, cudaStream_t st);
+cg_status check_status_word(uint32_t* status, cudaStream_t st);
+cg_status prepare_queries(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, bool reuse, cudaStream_t st);
+cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
+                      int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
+                      cudaStream_t st);
+cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
+                   double* d2, cudaStream_t st);
 cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
 cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
 cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,

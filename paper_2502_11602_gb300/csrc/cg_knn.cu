@@ -32,7 +32,6 @@
 
 namespace cg {
 
-cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st);
 
 namespace {
 
@@ -489,14 +488,14 @@ __global__ void knn_thr_tiles_kernel(Thresholds* out, const Tile* __restrict__ t
 
 }  // namespace
 
-cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, int k, int32_t* idx, double* d2,
+cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx, double* d2,
                    cudaStream_t st) {
   if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external k-NN queries on a batched index (every point queries its own tile)");
   if (!all_points) {
-    cg_status s = prepare_queries(ix, q, nq, st);
+    cg_status s = prepare_queries(ix, C, q, nq, false, st);
     if (s != CG_OK) return s;
   }
   if (nq == 0) return CG_OK;
@@ -508,7 +507,7 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
   cudaError_t e = cudaMemsetAsync(ctrs, 0, 256, st);
   double emax = 0;
   for (const Tile& T : ix->tiles_host) emax = std::max(emax, (double)T.enc_err);
-  knn_thr_kernel<<<1, 1, 0, st>>>(thr, emax, all_points ? nullptr : ix->plan.nblocks_dev + 4); note_launch();
+  knn_thr_kernel<<<1, 1, 0, st>>>(thr, emax, all_points ? nullptr : C.plan.nblocks_dev + 4); note_launch();
   QuerySet qs;
   if (all_points) {
     qs.all_points = 1;
@@ -520,7 +519,7 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
     qs.qrec64 = ix->pts64s;
     qs.q64 = ix->xyz64;
   } else {
-    QueryPlan& P = ix->plan;
+    QueryPlan& P = C.plan;
     if (P.nblocks_host_version != P.version) {
       if (e == cudaSuccess) e = cudaMemcpyAsync(&P.nblocks, P.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -544,13 +543,13 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
     const size_t smem = knn_smem<1>();
     cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, ix->status); note_launch();
+    knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status); note_launch();
     knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2); note_launch();
   } else {
     const size_t smem = knn_smem<0>();
     cudaFuncSetAttribute(knn_fast_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    knn_fast_kernel<0><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, ix->status); note_launch();
+    knn_fast_kernel<0><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status); note_launch();
     knn_slow_kernel<0><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2); note_launch();
   }
   e = cudaGetLastError();
@@ -559,6 +558,11 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
   return CG_OK;
 }
 
+
+cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, int k, int32_t* idx, double* d2,
+                   cudaStream_t st) {
+  return knn_pass(ix, ix->ctx, all_points, q, nq, k, idx, d2, st);
+}
 
 cg_status knn_work_alloc(cg_index* ix, KnnWork& w, cudaStream_t st) {
   w.slow = (uint32_t*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->n, 1), st);

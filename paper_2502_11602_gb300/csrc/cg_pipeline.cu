@@ -69,8 +69,7 @@ void teardown(cg_pipeline* p, cudaStream_t st) {
   p->knn_idx = nullptr;
   p->knn_d2 = nullptr;
   if (p->ix) {
-    p->ix->radius.bufs.release(st);
-    p->ix->plan.bufs.release(st);
+    p->ix->ctx.release(st);
     p->ix->bufs.release(st);
     delete p->ix;
     p->ix = nullptr;
@@ -95,8 +94,7 @@ cg_status setup(cg_pipeline* p, cudaStream_t st) {
   if (s == CG_OK) s = radius_work_alloc(ix, p->rw, p->bw.cap_keys, p->headroom, total, st);
   if (s == CG_OK && p->k > 0) s = knn_work_alloc(ix, p->kw, st);
   if (s != CG_OK) return s;
-  ix->radius.bufs.release(st);
-  ix->radius = RadiusState();
+  ix->ctx.release(st);
   // the caller's buffer stays valid for the pipeline's lifetime: the exact
   // binary64 rechecks read it in place instead of a copy
   ix->xyz64 = const_cast<double*>(p->xyz);

@@ -557,9 +557,11 @@ __global__ void replay_check_out_kernel(const int64_t* __restrict__ total, int64
 
 // -------------------------------------------------------------- host side
 
-cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st) {
-  QueryPlan& P = ix->plan;
-  if (P.q == q && P.nq == nq && P.nblocks_dev) return CG_OK;
+// reuse: keep the plan of the same query buffer (a fill after its count);
+// every other call plans again, as the buffer's contents may have changed.
+cg_status prepare_queries(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, bool reuse, cudaStream_t st) {
+  QueryPlan& P = C.plan;
+  if (reuse && P.q == q && P.nq == nq && P.nblocks_dev) return CG_OK;
   P.bufs.release(st);
   P.q = q;
   P.nq = nq;
@@ -590,15 +592,15 @@ cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_
   cudaError_t e = cudaMemsetAsync(P.nblocks_dev, 0, 64, st);
   if (nq > 0) {
     query_key_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, ix->tiles, ix->dim, keys,
-                                                         P.nblocks_dev + 4, ix->status); note_launch();
+                                                         P.nblocks_dev + 4, C.status); note_launch();
     const Tile& T = ix->tiles_host[0];
     int bits = 0;
     uint64_t kmax = (uint64_t)T.key_base + (uint64_t)T.n[0] * T.n[1] * T.n[2];
     while (bits < 32 && ((uint64_t)1 << bits) < kmax) ++bits;
-    if (e == cudaSuccess) e = radix_sort_pairs(keys, nq, bits, skeys, perm, sort_scratch, ix->status, st);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, nq, bits, skeys, perm, sort_scratch, C.status, st);
     query_gather_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, perm, ix->tiles, P.qrec, P.qrec64); note_launch();
     qrun_flag_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag); note_launch();
-    if (e == cudaSuccess) e = exclusive_scan_u32_u32(flag, rank, nq, scan_scratch, ix->status, st);
+    if (e == cudaSuccess) e = exclusive_scan_u32_u32(flag, rank, nq, scan_scratch, C.status, st);
     qrun_emit_kernel<<<grid_for(nq, 256), 256, 0, st>>>(skeys, nq, flag, rank, P.blk_key, P.blk_beg,
                                                         P.nblocks_dev); note_launch();
   }
@@ -622,11 +624,11 @@ cudaError_t launch_radius(const RadiusLaunch& L, uint32_t* counts, const int64_t
                           cudaStream_t st) {
   auto kern = radius_kernel<PREC, KERN, FILL>;
   const size_t smem = radius_smem<PREC>();
-  static bool configured = false;
-  if (!configured) {
+  static const bool configured = [&] {  // once per process, thread-safe
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = true;
-  }
+    return true;
+  }();
+  (void)configured;
   kern<<<grid, RT, smem, st>>>(L.iv, L.qs, L.thr, counts, offsets, out, heavy, work_ctr, status); note_launch();
   return cudaGetLastError();
 }
@@ -646,13 +648,12 @@ cudaError_t dispatch_radius(int prec, int kern, const RadiusLaunch& L, uint32_t*
 }
 
 int radius_grid(int prec) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, m = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    return m > 0 ? m : 152;
+  }();
   size_t smem = prec == CG_FP32_OFFSET ? radius_smem<1>() : radius_smem<0>();
   int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
   return sms * per_sm;
@@ -661,16 +662,17 @@ int radius_grid(int prec) {
 }  // namespace
 
 // Radius pass state kept on the index between the count and fill calls.
-cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, double r, int kernel,
-                      bool fill, int64_t* offsets, int32_t* out, int64_t* total_host, cudaStream_t st) {
+cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
+                      int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
+                      cudaStream_t st) {
   if (!(r > 0) || !isfinite(r)) return fail(CG_ERR_INVALID, "radius must be positive and finite");
   if (kernel != CG_SPHERE && kernel != CG_CUBE) return fail(CG_ERR_INVALID, "unknown kernel");
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
-  RadiusState& R = ix->radius;
+  RadiusState& R = C.radius;
   if (!all_points) {
-    cg_status s = prepare_queries(ix, q, nq, st);
+    cg_status s = prepare_queries(ix, C, q, nq, fill, st);
     if (s != CG_OK) return s;
   }
   // per-call device state (counts, heavy list, thresholds, counters)
@@ -691,7 +693,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     R.nq = nqq;
     R.r = r;
     R.kernel = kernel;
-    R.plan_version = ix->plan.version;
+    R.plan_version = C.plan.version;
     cudaError_t e = cudaMemsetAsync(R.ctrs, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
     double emax = 0;
@@ -702,13 +704,13 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
       static_assert(sizeof(th) <= sizeof(R.thr_host), "threshold copy");
       memcpy(R.thr_host, &th, sizeof th);
     } else {
-      thresholds_kernel<<<1, 1, 0, st>>>(R.thr, r, emax, ix->plan.nblocks_dev + 4); note_launch();
+      thresholds_kernel<<<1, 1, 0, st>>>(R.thr, r, emax, C.plan.nblocks_dev + 4); note_launch();
       e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(e, "thresholds");
   } else {
     if (!R.counts || R.all_points != all_points || R.q != q || R.nq != nqq || R.r != r ||
-        R.kernel != kernel || R.plan_version != ix->plan.version)
+        R.kernel != kernel || R.plan_version != C.plan.version)
       return fail(CG_ERR_INVALID, "radius fill without a matching count pass");
   }
   RadiusLaunch L;
@@ -724,7 +726,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     L.qs.qrec64 = ix->pts64s;
     L.qs.q64 = ix->xyz64;
   } else {
-    QueryPlan& P = ix->plan;
+    QueryPlan& P = C.plan;
     L.qs.all_points = 0;
     L.qs.nq = (uint32_t)nq;
     L.qs.nblocks = 0xffffffffu;  // read from the device below
@@ -750,13 +752,13 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
   if (!all_points) {
     // the block count lives on the device: copy it into the launch struct
     // through a tiny synchronous read only once per plan
-    if (ix->plan.nblocks_host_version != ix->plan.version) {
-      e = cudaMemcpyAsync(&ix->plan.nblocks, ix->plan.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
+    if (C.plan.nblocks_host_version != C.plan.version) {
+      e = cudaMemcpyAsync(&C.plan.nblocks, C.plan.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_fail(e, "query plan readback");
-      ix->plan.nblocks_host_version = ix->plan.version;
+      C.plan.nblocks_host_version = C.plan.version;
     }
-    L.qs.nblocks = ix->plan.nblocks;
+    L.qs.nblocks = C.plan.nblocks;
   }
   const int grid = radius_grid(ix->precision);
   if (nqq > 0 && L.qs.nblocks > 0) {
@@ -777,9 +779,9 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
         return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
       Lbig.qs.blk_list = R.big_list;
       e = launch_radius_plan(ix->precision, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
-                             R.ctrs + 12, ix->status, st);
-      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, ix->status, st);
-      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, ix->status, st);
+                             R.ctrs + 12, C.status, st);
+      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, C.status, st);
+      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, C.status, st);
       uint32_t tots[3] = {0, 0, 0};
       if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[0], R.moff + nb, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[1], R.idoff + nb, 4, cudaMemcpyDeviceToHost, st);
@@ -796,33 +798,33 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
         R.meta = (uint32_t*)R.bufs.get(16 * (size_t)nb, st);
         if (!R.meta) return fail(CG_ERR_OOM, "device allocation failed (radius meta)");
         e = launch_radius_count3(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks, R.ids,
-                                 R.meta, R.ctrs + 14, ix->status, st);
+                                 R.meta, R.ctrs + 14, C.status, st);
       } else {
         e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
-                                 R.masks, R.ids, R.ctrs + 14, ix->status, st);
+                                 R.masks, R.ids, R.ctrs + 14, C.status, st);
       }
       if (e == cudaSuccess && R.big_n > 0)
-        e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, ix->status,
+        e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, C.status,
                                    grid, st);
     } else {
       e = cudaMemsetAsync(R.ctrs + 16, 0, 4, st);
       if (e == cudaSuccess) {
         if (ix->precision == CG_FP32_OFFSET)
           e = launch_radius_fill3(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, R.meta, offsets, out,
-                                  R.ctrs + 16, ix->status, st);
+                                  R.ctrs + 16, C.status, st);
         else
           e = launch_radius_fill2(ix->precision, L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets,
-                                  out, R.ctrs + 16, ix->status, st);
+                                  out, R.ctrs + 16, C.status, st);
       }
       if (e == cudaSuccess && R.big_n > 0)
-        e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, ix->status, grid,
+        e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, C.status, grid,
                                   st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "radius kernel");
   }
   if (!fill) {
     if (nqq > 0) {
-      e = exclusive_scan_u32_i64(R.counts, offsets, nqq, R.scan_scratch, ix->status, st);
+      e = exclusive_scan_u32_i64(R.counts, offsets, nqq, R.scan_scratch, C.status, st);
     } else {
       e = cudaMemsetAsync(offsets, 0, 8, st);
     }
@@ -836,7 +838,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
       R.heavy_count = stats[0];
       R.heavy_scratch = ((uint64_t)stats[3] << 32) | stats[2];
       R.stats_known = true;
-      cg_status s = check_status(ix, st);
+      cg_status s = check_status_word(C.status, st);
       if (s != CG_OK) return s;
     } else {
       R.stats_known = false;
@@ -863,7 +865,7 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
     const size_t smem = 4 * kSmemSortCap;
     row_sort_kernel<<<grid_for(R.heavy_count, 1, 152 * 4), 512, smem, st>>>(
         R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch,
-        ix->status); note_launch();
+        C.status); note_launch();
     e = cudaGetLastError();
     if (scratch) dev_free(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "row sort");
@@ -872,11 +874,16 @@ cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq
 }
 
 
+cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, double r, int kernel,
+                      bool fill, int64_t* offsets, int32_t* out, int64_t* total_host, cudaStream_t st) {
+  return radius_pass(ix, ix->ctx, all_points, q, nq, r, kernel, fill, offsets, out, total_host, st);
+}
+
 // ------------------------------------------------- replayed (graph) pass
 
 cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,
                             cudaStream_t st) {
-  const RadiusState& R = ix->radius;
+  const RadiusState& R = ix->ctx.radius;
   const int64_t n = std::max<int64_t>(ix->n, 1);
   auto grow = [&](double v, double slack) { return v * headroom + slack; };
   w.cap_nb = std::max<uint32_t>(cap_nb, 1);

@@ -1383,13 +1383,12 @@ template <int PREC>
 size_t count2_smem() { return CountSmem<PREC>::A + CountSmem<PREC>::B + kCountTail; }
 
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, m = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    return m > 0 ? m : 152;
+  }();
   return sms;
 }
 

@@ -174,3 +174,23 @@ def test_tall_columns_and_stacked_layers(kernel):
     xyz = np.ascontiguousarray(np.concatenate([ground, roof] + poles) + [508000.0, 5440000.0, 0.0])
     for r in (0.4, 1.0, 2.5):
         _check(xyz, None, r, 1.0, kernel=kernel)
+
+
+def test_query_buffer_rewritten_in_place_is_planned_again():
+    # the same device buffer (same pointer, same size) with new contents must
+    # give the new contents' results, for radius search and k-NN alike
+    xyz = cloudgen.als_uniform(30_000, extent=(40.0, 40.0), seed=12)
+    ix = cg.Index(torch.from_numpy(xyz).to(DEV), 1.0)
+    ref = oracle.Index(xyz, 1.0)
+    rng = np.random.default_rng(5)
+    q = torch.empty((2000, 3), dtype=torch.float64, device=DEV)
+    for trial in range(3):
+        qh = xyz[rng.integers(0, len(xyz), 2000)] + rng.normal(0, 0.5, (2000, 3))
+        q.copy_(torch.from_numpy(qh))
+        off, ind = ix.radius_search(q, 1.2)
+        o_off, o_ind = ref.radius_search(qh, 1.2, threads=8)
+        assert np.array_equal(off.cpu().numpy(), o_off) and np.array_equal(ind.cpu().numpy(), o_ind)
+        idx, d2 = ix.knn(q, 8)
+        r_idx, r_d2 = ref.knn(qh, 8, threads=8)
+        assert np.array_equal(idx.cpu().numpy(), r_idx) and np.array_equal(d2.cpu().numpy(), r_d2)
+    ix.close()
