@@ -8,9 +8,14 @@ original id) at r = 1 m.  Inputs are resident in HBM when the timed region
 starts; they are 288 MB, larger than the 129 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tile|batched|serving]
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on
-the host cores instead (bounded sample of the same workload).
+the host cores instead (bounded sample of the same workload).  The other
+workloads: `batched` = 256 tiles (~60M points) through the graph-captured
+pipeline (build + radius r = 1 m + k-NN k = 16), binary32-offset and binary64
+storage side by side; `serving` = 8 resident indexes under a Poisson stream
+of radius / k-NN requests (p50 / p99 latency and queries/s).
 """
 from __future__ import annotations
 
@@ -199,6 +204,37 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def _alg_tests(xyz, r: float, cell: float) -> int:
+    """Candidate tests of Algorithm 1 with every point as a query on a 2D
+    dense grid: for each query, the points of every voxel that meets its
+    kernel's bounding box [c - r, c + r] in x and y (z is not indexed).
+    Counted with a summed-area table of the voxel counts."""
+    import numpy as np
+    lo = xyz[:, :2].min(0)
+    hi = xyz[:, :2].max(0)
+    nx, ny = (np.floor((hi - lo) / cell).astype(np.int64) + 1).tolist()
+    ij = np.floor((xyz[:, :2] - lo) / cell).astype(np.int64)
+    cnt = np.bincount(ij[:, 0] * ny + ij[:, 1], minlength=nx * ny).reshape(nx, ny)
+    sat = np.zeros((nx + 1, ny + 1), np.int64)
+    sat[1:, 1:] = cnt.cumsum(0).cumsum(1)
+    total = 0
+    for a in range(0, len(xyz), 4_000_000):
+        c = xyz[a:a + 4_000_000, :2]
+        i0 = np.clip(np.floor((c[:, 0] - r - lo[0]) / cell).astype(np.int64), 0, nx - 1)
+        i1 = np.clip(np.floor((c[:, 0] + r - lo[0]) / cell).astype(np.int64), 0, nx - 1)
+        j0 = np.clip(np.floor((c[:, 1] - r - lo[1]) / cell).astype(np.int64), 0, ny - 1)
+        j1 = np.clip(np.floor((c[:, 1] + r - lo[1]) / cell).astype(np.int64), 0, ny - 1)
+        total += int((sat[i1 + 1, j1 + 1] - sat[i0, j1 + 1] - sat[i1 + 1, j0] + sat[i0, j0]).sum())
+    return total
+
+
+# binary32 lane operations of one sphere test: 3 subtractions, 1 multiply,
+# 2 fused multiply-adds, 1 comparison
+OPS_PER_TEST = 7
+COUNT_PHASES = ("radius_count4", "radius_count3", "radius_count2", "radius_v1_count")
+FILL_PHASES = ("radius_fill3", "radius_fill2", "radius_v1_fill", "radius_row_sort")
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -222,10 +258,10 @@ def run_ours(args):
 
     prec = cg.FP32_OFFSET if args.precision == "fp32" else cg.FP64
 
-    def step(record=None):
+    def step(record=None, p=prec):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record is not None else None
         if ev: ev[0].record(stream)
-        h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, prec)
+        h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, p)
         if ev: ev[1].record(stream)
         off = torch.empty(n + 1, dtype=torch.int64, device=dev)
         total = cg.cg_all_points_count(h, RADIUS, cg.SPHERE, off)
@@ -248,6 +284,8 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    cg.cg_profile_read(reset=True)
+    cg.cg_profile_enable(True)
     launches0 = cg.cg_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -257,6 +295,8 @@ def run_ours(args):
     t1.record(stream)
     torch.cuda.synchronize()
     launches = (cg.cg_launch_count() - launches0) / args.steps
+    cg.cg_profile_enable(False)
+    phases = cg.cg_profile_read(reset=True)
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
@@ -295,23 +335,61 @@ def run_ours(args):
 
     value = world * n / (ms * 1e-3)
     peak, peak_kind = _peaks()
-    # dominant kernel: the fill pass (largest share of the step)
-    stages = {"build": build_ms, "count": count_ms, "fill": fill_ms}
-    dom = max(("count", "fill"), key=lambda s: stages[s])
-    bytes_per_point = 16  # binary32 record: x~, y~, z~, id
-    info_ncell = int(math.floor(side / CELL) + 1) ** 2
-    if dom == "fill":
-        alg = bytes_per_point * n + 4 * (info_ncell + 1) + 8 * (n + 1) + 4 * total
-        kname, files = "radius_fill", ["cg_query.cu", "cg_internal.cuh"]
-        dur = fill_ms
+    per_step = {k: v[1] / args.steps for k, v in phases.items()}
+    count_k = sum(per_step.get(k, 0.0) for k in COUNT_PHASES)
+    fill_k = sum(per_step.get(k, 0.0) for k in FILL_PHASES)
+    ncell = int(math.floor((xyz[:, 0].max() - xyz[:, 0].min()) / CELL) + 1) * \
+        int(math.floor((xyz[:, 1].max() - xyz[:, 1].min()) / CELL) + 1)
+    if count_k >= fill_k:
+        # the count kernels are bound by the binary32 tests, not by memory
+        tests = _alg_tests(xyz, RADIUS, CELL)
+        sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
+        alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
+        achieved = OPS_PER_TEST * tests / (count_k * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "+".join(k for k in COUNT_PHASES if k in per_step),
+                "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s", "frac": achieved / alu_peak,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+                "traffic": _traffic("radius_count4", ["cg_radius2.cu", "cg_query.cuh", "cg_internal.cuh"]),
+                "algorithmic_tests": tests, "ops_per_test": OPS_PER_TEST, "ms_per_launch": count_k}
     else:
-        alg = bytes_per_point * n + 4 * (info_ncell + 1) + 4 * n + 16 * (n + 1)
-        kname, files = "radius_count", ["cg_query.cu", "cg_internal.cuh"]
-        dur = count_ms
-    achieved = alg / (dur * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(kname, files),
-            "algorithmic_bytes": alg, "ms_per_launch": dur}
+        alg = 16 * n + 4 * (ncell + 1) + 8 * (n + 1) + 4 * total
+        achieved = alg / (fill_k * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "+".join(k for k in FILL_PHASES if k in per_step),
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": _traffic("radius_fill3", ["cg_radius2.cu", "cg_query.cuh", "cg_internal.cuh"]),
+                "algorithmic_bytes": alg, "ms_per_launch": fill_k}
+
+    # secondary measurements on the same tile: k-NN (k = 16) and the binary64 path
+    h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, prec)
+    kidx = torch.empty((n, 16), dtype=torch.int32, device=dev)
+    kd2 = torch.empty((n, 16), dtype=torch.float64, device=dev)
+    kt = []
+    for it in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cg.cg_all_points_knn(h, 16, kidx, kd2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if it > 0:
+            kt.append(a.elapsed_time(b))
+    cg.cg_index_status(h)
+    cg.cg_index_free(h)
+    del kidx, kd2
+    fp64_ms = None
+    if prec == cg.FP32_OFFSET and not args.no_fp64:
+        step(p=cg.FP64)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            step(p=cg.FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = a.elapsed_time(b) / 2
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -320,13 +398,228 @@ def run_ours(args):
                    "n_points": n, "radius_m": RADIUS, "cell_m": CELL, "precision": args.precision,
                    "l2": "inputs larger than L2 (288 MB points, 129 MB L2)", "parallelism": f"replicas x{world}"},
         "neighbors_per_s": world * total / (ms * 1e-3), "neighbors_per_step": total,
-        "stages_ms": stages,
+        "stages_ms": {"build": build_ms, "count": count_ms, "fill": fill_ms},
+        "kernels_ms_per_step": per_step,
         "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": (n + 1) * 8 + total * 4},
         "roofline": roof, "clocks": clk, "gpu_launches": launches,
+        "knn16": {"queries_per_s": world * n / (statistics.mean(kt) * 1e-3), "ms": statistics.mean(kt)},
     }
+    if fp64_ms is not None:
+        line["fp64_path"] = {"queries_per_s": world * n / (fp64_ms * 1e-3), "ms_per_step": fp64_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(xyz, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batched(args):
+    """256 tiles (~60M points) through the graph-captured pipeline: build +
+    all-points radius r = 1 m + all-points k-NN k = 16, one graph replay per
+    step, binary32-offset storage against binary64 storage."""
+    import numpy as np
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+    from paper_2502_11602_gb300 import autotune
+
+    rank, world, local, dist = _setup_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    xyz, off = cloudgen.batched_tiles(args.tiles, args.batch_points, seed=cloudgen.CONFIG_SEED + 3 + 1000 * rank)
+    n = len(xyz)
+    x = torch.from_numpy(xyz).to(dev)
+    cells, report = autotune.tune(xyz, off, radius=1.0, k=16, precision=cg.FP32_OFFSET,
+                                  cache_path=os.path.join(ROOT, "_build", "autotune.json"))
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, prec in (("fp32", cg.FP32_OFFSET), ("fp64", cg.FP64)):
+        pipe = cg.Pipeline(x, off, cells, radius=1.0, k=16, precision=prec)
+        for _ in range(args.warmup):
+            total = pipe.run()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = cg.cg_launch_count()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            pipe.run(sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        launches = (cg.cg_launch_count() - l0) / args.steps
+        total = pipe.run()  # synchronising check: no re-plan, no device error
+        assert pipe.info()["replans"] == 0
+        ms = a.elapsed_time(b) / args.steps
+        if dist is not None:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        info = pipe.info()
+        # end to end: pinned host points in, CSR and k-NN out, every step
+        host_in = torch.from_numpy(xyz).pin_memory()
+        outs = pipe.outputs()
+        host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+        et = []
+        for it in range(3):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x.copy_(host_in, non_blocking=True)
+            t = pipe.run()
+            o = pipe.outputs()
+            for k, v in o.items():
+                host[k][:v.shape[0]].copy_(v, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                et.append(e0.elapsed_time(e1))
+        e2e_ms = statistics.mean(et)
+        out[name] = {"ms_per_step": ms, "queries_per_s": world * n / (ms * 1e-3),
+                     "neighbors_per_s": world * total / (ms * 1e-3), "neighbors_per_step": total,
+                     "graph_kernels": info["graph_kernels"], "gpu_launches": launches,
+                     "device_bytes": info["device_bytes"],
+                     "e2e_ms": e2e_ms, "e2e_queries_per_s": world * n / (e2e_ms * 1e-3),
+                     "d2h_bytes": int(sum(v.numel() * v.element_size() for v in o.values()))}
+        pipe.close()
+        del host_in, host, outs, o
+    clk = clocks.stop()
+    f = out["fp32"]
+    line = {
+        "metric": "batched radius+kNN queries/s (256 ALS tiles, ~60M pts, r=1 m, k=16, one graph replay per step)",
+        "value": f["queries_per_s"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.tiles} ALS-like tiles, {n} pts, density 5-60 pts/m2, log-uniform sizes "
+                               "10k-2M, 2D dense grids, cell autotuned per density bucket, sphere r=1 m, k=16",
+                   "n_points": n, "tiles": args.tiles, "cells_used": sorted(set(cells.tolist())),
+                   "autotune_report": {str(k): v for k, v in report.items()},
+                   "l2": "inputs larger than L2 (1.4 GB points)"},
+        "fp32_offset": f, "fp64": out["fp64"],
+        "fp32_over_fp64": out["fp64"]["ms_per_step"] / f["ms_per_step"],
+        "e2e": {"value": f["e2e_queries_per_s"], "unit": "queries/s", "h2d_bytes_per_step": n * 24,
+                "d2h_bytes_per_step": f["d2h_bytes"]},
+        "clocks": clk, "gpu_launches": f["gpu_launches"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_serving(args):
+    """8 resident indexes (ALS and TLS clouds of 5-30M points, binary32
+    offsets) under a Poisson stream of requests: query sets of log-uniform
+    size in [1k, 1M] drawn from the index's points, each a sphere radius
+    (U[0.25, 3] m on ALS, U[0.05, 0.5] m on TLS) or a k-NN with k in
+    {8, 16, 32} (even odds).  Offered load
+    swept in steps up to saturation; p50 / p99 latency and queries/s."""
+    import numpy as np
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+
+    rank, world, local, dist = _setup_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(cloudgen.CONFIG_SEED + 4 + 1000 * rank)
+    sizes = [int(v) for v in np.round(np.exp(rng.uniform(np.log(5e6), np.log(30e6), 8)) * args.serve_scale)]
+    clouds, indexes, cells = [], [], []
+    for i, m in enumerate(sizes):
+        if i % 2 == 0:
+            side = 500.0 * math.sqrt(m / N_POINTS)
+            c = cloudgen.als_urban(m, extent=(side, side), seed=cloudgen.CONFIG_SEED + 40 + i,
+                                   n_buildings=max(1, round(200 * m / N_POINTS)),
+                                   n_trees=max(1, round(3000 * m / N_POINTS)))
+            cell, dim = 1.0, 2
+        else:
+            c = cloudgen.tls_street(m, seed=cloudgen.CONFIG_SEED + 40 + i)
+            cell, dim = 0.25, 3
+        x = torch.from_numpy(c).to(dev)
+        indexes.append(cg.Index(x, cell, cell, dim=dim, precision=cg.FP32_OFFSET))
+        clouds.append(x)
+        cells.append(cell)
+    # requests, queries staged on the device beforehand
+    nreq = args.serve_requests
+    reqs = []
+    for i in range(nreq):
+        j = int(rng.integers(0, 8))
+        nq = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        sel = torch.from_numpy(rng.integers(0, clouds[j].shape[0], nq)).to(dev)
+        q = clouds[j][sel].contiguous()
+        if rng.random() < 0.5:
+            # ALS indexes: r ~ U[0.25, 3] m; TLS indexes (3D, up to 250k
+            # pts/m^2 near a scanner): the TLS radii, r ~ U[0.05, 0.5] m
+            r = float(rng.uniform(0.25, 3.0)) if j % 2 == 0 else float(rng.uniform(0.05, 0.5))
+            reqs.append((j, q, "radius", r))
+        else:
+            reqs.append((j, q, "knn", int(rng.choice([8, 16, 32]))))
+    torch.cuda.synchronize()
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def run_at(rate):
+        import threading
+        srv = cg.Server(indexes, slots=args.serve_slots, memory_budget=budget)
+        gaps = rng.exponential(1.0 / rate, nreq)
+        ids = []
+        done = []
+
+        def submitter():
+            t = time.perf_counter()
+            for (j, q, kind, p), g in zip(reqs, gaps):
+                t += g
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids.append(srv.submit_radius(j, q, p) if kind == "radius" else srv.submit_knn(j, q, p))
+
+        th = threading.Thread(target=submitter)
+        t0 = time.perf_counter()
+        th.start()
+        failed = 0
+        for _ in range(nreq):
+            rid = srv.wait_any()
+            try:
+                srv.wait(rid, copy=False)
+            except cg.CheeseError:
+                failed += 1
+            srv.release(rid)
+            done.append(time.perf_counter())
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return {"offered_req_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "queries_per_s": st["queries_per_s"], "requests": st["requests_done"], "failed": failed,
+                "max_in_flight": st["max_in_flight"], "preemptions": st["preemptions"],
+                "memory_peak_gb": st["memory_peak"] / 2 ** 30, "wall_s": wall}
+
+    # warm-up, then a closed burst (everything at once) gives the capacity
+    run_at(1e6)
+    sat = run_at(1e6)
+    cap_rps = sat["requests"] / max(sat["wall_s"], 1e-9)
+    sweep = [run_at(f * cap_rps) for f in (0.25, 0.5, 0.75, 0.9)]
+    line = {
+        "metric": "serving queries/s and p50/p99 latency (8 resident indexes, Poisson radius/kNN requests)",
+        "value": sat["queries_per_s"], "unit": "queries/s", "n_gpus": world, "steps": nreq, "warmup": nreq,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "8 indexes (4 ALS 2D cell 1 m, 4 TLS 3D cell 0.25 m), binary32 offsets; requests "
+                               "nq log-uniform [1k, 1M], r ~ U[0.25, 3] m (ALS) / U[0.05, 0.5] m (TLS) or "
+                               "k in {8,16,32}",
+                   "index_points": sizes, "slots": args.serve_slots, "memory_budget_gb": args.serve_budget_gb},
+        "saturation": sat, "sweep": sweep,
+    }
+    for ix in indexes:
+        ix.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -344,9 +637,24 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS, help="tile size (profiling cases only)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison on the tile")
+    ap.add_argument("--workload", choices=["tile", "batched", "serving"], default="tile")
+    ap.add_argument("--tiles", type=int, default=256)
+    ap.add_argument("--batch-points", type=int, default=60_000_000)
+    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="index sizes x this (smaller test runs)")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload != "tile":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the tile workload only"}))
+            return
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -417,6 +417,19 @@ cg_status cg_server_stats(cg_server_t server, cg_server_stats_t* stats);
    call on this server. */
 cg_status cg_server_free(cg_server_t server);
 
+/*
+ * Device-time tracing (diagnostics; no counterpart in the paper).  While
+ * enabled, the library brackets each of its kernel phases (build steps,
+ * radius plan / count / fill / row order, k-NN, sorts and scans) with CUDA
+ * events on the launching stream; launches inside a graph capture are not
+ * traced.  cg_profile_read waits for the recorded events and writes a JSON
+ * object {"phase": [launches, total_ms], ...} into buf (len receives the
+ * size needed, NUL included; buf NULL only queries the size); reset != 0
+ * clears the totals.  Tracing adds two event records per phase.
+ */
+cg_status cg_profile_enable(int on);
+cg_status cg_profile_read(char* buf, size_t cap, size_t* len, int reset);
+
 #ifdef __cplusplus
 }
 #endif

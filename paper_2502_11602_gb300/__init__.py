@@ -32,7 +32,8 @@ EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
            "cg_all_points_knn", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
            "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free", "cg_server_create", "cg_server_submit",
-           "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free"]
+           "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free",
+           "cg_profile_enable", "cg_profile_read"]
 
 REQ_RADIUS, REQ_KNN = 0, 1
 
@@ -141,6 +142,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_server_release": [P, I64],
             "cg_server_stats": [P, P],
             "cg_server_free": [P],
+            "cg_profile_enable": [I],
+            "cg_profile_read": [P, ctypes.c_size_t, P, I],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -308,6 +311,21 @@ def _view(ptr: int, shape, typestr: str, device) -> torch.Tensor:
         dt = {"<i8": torch.int64, "<i4": torch.int32, "<f8": torch.float64}[typestr]
         return torch.empty(shape, dtype=dt, device=device)
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=device)
+
+
+def cg_profile_enable(on: bool = True):
+    """Device-time tracing of the library's kernel phases (CUDA events)."""
+    _check(load().cg_profile_enable(1 if on else 0))
+
+
+def cg_profile_read(reset: bool = True) -> dict:
+    """{phase: (launches, total_ms)} since the last reset (waits for the GPU)."""
+    import json
+    n = ctypes.c_size_t(0)
+    _check(load().cg_profile_read(None, 0, ctypes.byref(n), 0))
+    buf = ctypes.create_string_buffer(n.value + 256)
+    _check(load().cg_profile_read(buf, len(buf), ctypes.byref(n), 1 if reset else 0))
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
 # ------------------------------------------------------------- convenience

@@ -1,0 +1,101 @@
+"""Cell-size autotuner for batched tiles.
+
+Tiles are grouped by point density (points per m^2 of their xy bounding box,
+one bucket per factor of two).  For every bucket not yet in the cache, one
+representative tile (the bucket's median size) is indexed and searched at
+each candidate cell size through the library (build + all-points radius
+count and fill, plus k-NN when k > 0), and the fastest cell size is kept.
+Results are cached in a JSON file keyed by GPU name, dimension, radius,
+kernel, k, precision and bucket, so later runs make no measurement.
+
+The cell size only changes speed: the neighbour sets are fixed by the
+predicate, whatever the grid (Section 3: any voxel size gives the same
+kernel search result).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import torch
+
+CANDIDATES = (0.5, 1.0, 2.0)
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(base, "cheesegpu", "autotune.json")
+
+
+def density_bucket(xyz: np.ndarray) -> int:
+    """floor(log2(points per m^2 of the xy bounding box))."""
+    ext = xyz[:, :2].max(0) - xyz[:, :2].min(0)
+    area = max(float(ext[0]) * float(ext[1]), 1e-6)
+    return int(math.floor(math.log2(max(len(xyz) / area, 1e-6))))
+
+
+def _key(gpu: str, dim: int, radius: float, kernel: int, k: int, precision: int, bucket: int) -> str:
+    return f"{gpu}|dim{dim}|r{radius:g}|kern{kernel}|k{k}|prec{precision}|d{bucket}"
+
+
+def _time_cell(cg, tile: torch.Tensor, cell: float, dim: int, radius: float, kernel: int, k: int,
+               precision: int, reps: int = 3) -> float:
+    times = []
+    for it in range(reps + 1):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ix = cg.Index(tile, cell, cell, dim=dim, precision=precision)
+        ix.radius_search(None, radius, kernel, check=False)
+        if k > 0:
+            ix.knn(None, k, check=False)
+        b.record()
+        torch.cuda.synchronize()
+        ix.close()
+        if it > 0:
+            times.append(a.elapsed_time(b))
+    return float(np.median(times))
+
+
+def tune(xyz: np.ndarray, tile_offsets, radius: float, kernel: int = 0, k: int = 0, dim: int = 2,
+         precision: int = 1, candidates=CANDIDATES, cache_path: str | None = None,
+         device: str = "cuda:0") -> tuple[np.ndarray, dict]:
+    """Cell size per tile, and a report {bucket: {cell: ms, ..., "best": cell}}
+    for the buckets measured by this call (cached buckets are not re-timed)."""
+    import paper_2502_11602_gb300 as cg
+
+    off = np.asarray(tile_offsets, dtype=np.int64)
+    T = len(off) - 1
+    cache_path = cache_path or default_cache_path()
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    gpu = torch.cuda.get_device_name(torch.device(device))
+    buckets = np.array([density_bucket(xyz[off[t]:off[t + 1]]) for t in range(T)])
+    report = {}
+    for bk in sorted(set(buckets.tolist())):
+        key = _key(gpu, dim, radius, kernel, k, precision, bk)
+        if key in cache:
+            continue
+        members = np.nonzero(buckets == bk)[0]
+        sizes = off[members + 1] - off[members]
+        rep = int(members[np.argsort(sizes)[len(sizes) // 2]])
+        tile = torch.from_numpy(np.ascontiguousarray(xyz[off[rep]:off[rep + 1]])).to(device)
+        ms = {str(c): _time_cell(cg, tile, float(c), dim, radius, kernel, k, precision) for c in candidates}
+        best = float(min(ms, key=ms.get))
+        cache[key] = best
+        report[bk] = dict(ms, best=best, tile=rep, points=int(off[rep + 1] - off[rep]))
+        del tile
+    if report:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    cells = np.array([cache[_key(gpu, dim, radius, kernel, k, precision, int(b))] for b in buckets])
+    return cells, report

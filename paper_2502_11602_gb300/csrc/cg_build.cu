@@ -351,6 +351,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_CUDA(cudaMemcpyAsync(toff_dev, toff_host, sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
   bbox_init_kernel<<<(6 * ntiles + 255) / 256, 256, 0, st>>>(bb, ntiles); note_launch();
   {
+    ProfScope prof("build_bbox", st);
     int64_t blocks = (n + kThreads * kBoxItems - 1) / (kThreads * kBoxItems);
     bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, toff_dev, ntiles, bb, ix->status); note_launch();
   }
@@ -419,7 +420,10 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_ALLOC(skeys, uint32_t, n, tmp);
   CG_ALLOC(perm, uint32_t, n, ix->bufs);  // kept: original id of every sorted position
   ix->sid = perm;
-  key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, ntiles, dim, keys); note_launch();
+  {
+    ProfScope prof("build_keys", st);
+    key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, ntiles, dim, keys); note_launch();
+  }
   CG_CUDA(cudaGetLastError());
 
   // B3: stable radix sort of (key, id)
@@ -427,15 +431,21 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   while (bits < 32 && ((uint64_t)1 << bits) < key_base) ++bits;
   void* sort_scratch;
   CG_ALLOC(sort_scratch, char, radix_sort_scratch_bytes(n), tmp);
-  CG_CUDA(radix_sort_pairs(keys, n, bits, skeys, perm, sort_scratch, ix->status, st));
+  {
+    ProfScope prof("build_sort", st);
+    CG_CUDA(radix_sort_pairs(keys, n, bits, skeys, perm, sort_scratch, ix->status, st));
+  }
 
   // B4: records and the exact binary64 copy in original order
   CG_ALLOC(ix->xyz64, double, 3 * n, ix->bufs);
   CG_CUDA(cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
   if (precision == CG_FP32_OFFSET) CG_ALLOC(ix->pts32, float4, n, ix->bufs);
   else CG_ALLOC(ix->pts64s, double4_32a, n, ix->bufs);
-  gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, perm, skeys, ix->tiles, ntiles,
-                                                             ix->pts32, ix->pts64s); note_launch();
+  {
+    ProfScope prof("build_gather", st);
+    gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, perm, skeys, ix->tiles, ntiles,
+                                                               ix->pts32, ix->pts64s); note_launch();
+  }
   CG_CUDA(cudaGetLastError());
 
   // runs of equal keys: the sorted unique-key table
@@ -444,8 +454,11 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_ALLOC(rank, uint32_t, n + 1, tmp);
   void* scan_scratch;
   CG_ALLOC(scan_scratch, char, scan_scratch_bytes(std::max<int64_t>(n, key_base + 1)), tmp);
-  run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag); note_launch();
-  CG_CUDA(exclusive_scan_u32_u32(flag, rank, n, scan_scratch, ix->status, st));
+  {
+    ProfScope prof("build_runs", st);
+    run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(skeys, n, flag); note_launch();
+    CG_CUDA(exclusive_scan_u32_u32(flag, rank, n, scan_scratch, ix->status, st));
+  }
   uint32_t m = 0;
   CG_CUDA(cudaMemcpyAsync(&m, rank + n, 4, cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
@@ -461,6 +474,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
     uint32_t* cnt;
     CG_ALLOC(cnt, uint32_t, key_base, tmp);
     CG_ALLOC(ix->cstart, uint32_t, key_base + 1, ix->bufs);
+    ProfScope prof("build_cells", st);
     CG_CUDA(cudaMemsetAsync(cnt, 0, 4 * key_base, st));
     voxel_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, m, cnt); note_launch();
     CG_CUDA(exclusive_scan_u32_u32(cnt, ix->cstart, (int64_t)key_base, scan_scratch, ix->status, st));

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +33,68 @@ void* g_user = nullptr;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+struct ProfPending {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+std::vector<ProfPending> g_prof_pending;
+std::map<std::string, std::pair<int64_t, double>> g_prof_acc;  // launches, total ms
+
+// Folds finished event pairs into the totals (waits for them).
+void prof_resolve() {
+  std::vector<ProfPending> p;
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    p.swap(g_prof_pending);
+  }
+  for (auto& r : p) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      std::lock_guard<std::mutex> g(g_prof_mu);
+      auto& e = g_prof_acc[r.name];
+      e.first += 1;
+      e.second += ms;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  cudaGetLastError();
+}
+}  // namespace
+
+ProfScope::ProfScope(const char* nm, cudaStream_t s) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  if (cudaEventCreate(&a) != cudaSuccess) {
+    a = nullptr;
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(a, s);
+  name = nm;
+  st = s;
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t b = nullptr;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(b, st);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof_pending.push_back({name, a, b});
+}
 
 void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
@@ -122,6 +186,34 @@ const char* cg_last_error(void) { return g_last_error.c_str(); }
 const char* cg_version(void) { return "cheesegpu 0.1 (sm_103a)"; }
 
 uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+cg_status cg_profile_enable(int on) {
+  if (!on) prof_resolve();
+  g_prof_on.store(on != 0);
+  return CG_OK;
+}
+
+cg_status cg_profile_read(char* buf, size_t cap, size_t* len, int reset) {
+  prof_resolve();
+  std::string out = "{";
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    bool first = true;
+    char tmp[256];
+    for (auto& kv : g_prof_acc) {
+      snprintf(tmp, sizeof tmp, "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(),
+               (long long)kv.second.first, kv.second.second);
+      out += tmp;
+      first = false;
+    }
+    if (reset) g_prof_acc.clear();
+  }
+  out += "}";
+  if (len) *len = out.size() + 1;
+  if (!buf || cap < out.size() + 1) return buf ? fail(CG_ERR_INVALID, "profile buffer too small") : CG_OK;
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return CG_OK;
+}
 
 cg_status cg_build(const double* xyz_dev, int64_t n, double cell_xy, double cell_z, int dim,
                    cg_flavor flavor, cg_precision precision, void* stream, cg_index_t* out) {

@@ -54,6 +54,20 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 // Counts kernel launches made by the library (host side, diagnostics).
 void note_launch(int n = 1);
 
+// Device-time tracing of the library's kernels (off unless enabled through
+// cg_profile_enable): a scope records CUDA events around the launches it
+// encloses on their stream; nothing is recorded while a stream is being
+// captured into a graph.
+struct ProfScope {
+  ProfScope(const char* name, cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+  const char* name = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr;
+};
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;

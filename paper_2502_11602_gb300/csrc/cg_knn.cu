@@ -543,14 +543,30 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
     const size_t smem = knn_smem<1>();
     cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status); note_launch();
-    knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2); note_launch();
+    {
+      ProfScope prof("knn_fast", st);
+      knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status);
+    }
+    note_launch();
+    {
+      ProfScope prof("knn_slow", st);
+      knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2);
+    }
+    note_launch();
   } else {
     const size_t smem = knn_smem<0>();
     cudaFuncSetAttribute(knn_fast_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    knn_fast_kernel<0><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status); note_launch();
-    knn_slow_kernel<0><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2); note_launch();
+    {
+      ProfScope prof("knn_fast", st);
+      knn_fast_kernel<0><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status);
+    }
+    note_launch();
+    {
+      ProfScope prof("knn_slow", st);
+      knn_slow_kernel<0><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2);
+    }
+    note_launch();
   }
   e = cudaGetLastError();
   tmp.release(st);

@@ -590,6 +590,7 @@ cg_status prepare_queries(cg_index* ix, QueryCtx& C, const double* q, int64_t nq
       !P.blk_key || !P.nblocks_dev || (!P.qrec && !P.qrec64))
     return bail(CG_ERR_OOM, "device allocation failed (query plan)");
   cudaError_t e = cudaMemsetAsync(P.nblocks_dev, 0, 64, st);
+  ProfScope prof("query_plan", st);
   if (nq > 0) {
     query_key_kernel<<<grid_for(nq, 256), 256, 0, st>>>(q, nq, ix->tiles, ix->dim, keys,
                                                          P.nblocks_dev + 4, C.status); note_launch();
@@ -629,6 +630,7 @@ cudaError_t launch_radius(const RadiusLaunch& L, uint32_t* counts, const int64_t
     return true;
   }();
   (void)configured;
+  ProfScope prof(FILL ? "radius_v1_fill" : "radius_v1_count", st);
   kern<<<grid, RT, smem, st>>>(L.iv, L.qs, L.thr, counts, offsets, out, heavy, work_ctr, status); note_launch();
   return cudaGetLastError();
 }
@@ -824,6 +826,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
   }
   if (!fill) {
     if (nqq > 0) {
+      ProfScope prof("offsets_scan", st);
       e = exclusive_scan_u32_i64(R.counts, offsets, nqq, R.scan_scratch, C.status, st);
     } else {
       e = cudaMemsetAsync(offsets, 0, 8, st);
@@ -863,6 +866,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       if (!scratch) return fail(CG_ERR_OOM, "device allocation failed (row sort scratch)");
     }
     const size_t smem = 4 * kSmemSortCap;
+    ProfScope prof("radius_row_sort", st);
     row_sort_kernel<<<grid_for(R.heavy_count, 1, 152 * 4), 512, smem, st>>>(
         R.heavy_list, R.heavy_soff, R.ctrs + 0, (uint32_t)std::max<int64_t>(nqq, 1), offsets, out, scratch,
         C.status); note_launch();

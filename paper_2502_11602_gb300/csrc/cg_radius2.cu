@@ -1408,6 +1408,7 @@ cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
                                uint32_t* big_n, const uint32_t* status, cudaStream_t st) {
   const int grid = (int)std::min<int64_t>((qs.nblocks + 3) / 4 + 1, (int64_t)sm_count() * 16);
+  ProfScope prof("radius_plan", st);
   if (prec == CG_FP32_OFFSET)
     radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status);
   else
@@ -1424,6 +1425,7 @@ cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const 
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)iv.n) ++bits;
   int passes = (bits + 7) / 8;
   if ((passes & 1) == 0) ++passes;
+  ProfScope prof("radius_count2", st);
 #define CG_LAUNCH_C2(P, KN)                                                                      \
   do {                                                                                           \
     auto kfn = radius_count2_kernel<P, KN>;                                                      \
@@ -1446,6 +1448,7 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                 const uint32_t* status, cudaStream_t st) {
+  ProfScope prof("radius_fill2", st);
   if (prec == CG_FP32_OFFSET) {
     auto kfn = radius_fill2_kernel<1>;
     kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
@@ -1467,6 +1470,7 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
   do {                                                                                                    \
     auto kfn = radius_count3_kernel<KN, TPB, KWc>;                                                        \
     const size_t smem = Count3Smem<KWc>::total;                                                            \
+    ProfScope prof("radius_count3", st);                                                                 \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
     kfn<<<resident_grid(kfn, TPB, smem), TPB, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, \
                                                           ids, meta, WORK, status, CLS);                   \
@@ -1476,15 +1480,21 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
   if (kern == CG_SPHERE) {
     auto k4 = radius_count4_kernel<CG_SPHERE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
-    k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                  ids, meta, work, status);
+    {
+      ProfScope prof("radius_count4", st);
+      k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
+                                                                    ids, meta, work, status);
+    }
     note_launch();
     CG_C3(CG_SPHERE, 256, 2048, 1u, work + 1);
   } else {
     auto k4 = radius_count4_kernel<CG_CUBE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
-    k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                  ids, meta, work, status);
+    {
+      ProfScope prof("radius_count4", st);
+      k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
+                                                                    ids, meta, work, status);
+    }
     note_launch();
     CG_C3(CG_CUBE, 256, 2048, 1u, work + 1);
   }
@@ -1497,6 +1507,7 @@ cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const B
                                 const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
                                 unsigned* work, const uint32_t* status, cudaStream_t st) {
   auto kfn = radius_fill3_kernel<256>;
+  ProfScope prof("radius_fill3", st);
   kfn<<<resident_grid(kfn, 256, 0), 256, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, meta, offsets, out, work,
                                                    status);
   note_launch();
