@@ -274,13 +274,17 @@ def run_ours(args):
             record.append(ev)
         return total
 
+    # the sampler starts before the warm-up: nvidia-smi's start-up stalls
+    # CUDA calls of this process for tens of ms and must not fall in the
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
     for _ in range(args.warmup):
         total = step()
     torch.cuda.synchronize()
 
     records = []
-    clocks = ClockSampler(local)
-    clocks.start()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -438,6 +442,7 @@ def run_batched(args):
     out = {}
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(1.0)
     for name, prec in (("fp32", cg.FP32_OFFSET), ("fp64", cg.FP64)):
         pipe = cg.Pipeline(x, off, cells, radius=1.0, k=16, precision=prec)
         for _ in range(args.warmup):

@@ -1470,10 +1470,11 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
   do {                                                                                                    \
     auto kfn = radius_count3_kernel<KN, TPB, KWc>;                                                        \
     const size_t smem = Count3Smem<KWc>::total;                                                            \
-    ProfScope prof("radius_count3", st);                                                                 \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                   \
-    kfn<<<resident_grid(kfn, TPB, smem), TPB, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, \
-                                                          ids, meta, WORK, status, CLS);                   \
+    const int g3 = resident_grid(kfn, TPB, smem);                                                        \
+    ProfScope prof("radius_count3", st);                                                                 \
+    kfn<<<g3, TPB, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,                           \
+                               ids, meta, WORK, status, CLS);                                            \
     note_launch();                                                                                        \
   } while (0)
   const size_t smem4 = sizeof(Count4Warp) * W4;
@@ -1481,9 +1482,9 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
     auto k4 = radius_count4_kernel<CG_SPHERE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
     {
+      const int g4 = resident_grid(k4, W4 * 32, smem4);
       ProfScope prof("radius_count4", st);
-      k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                    ids, meta, work, status);
+      k4<<<g4, W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, ids, meta, work, status);
     }
     note_launch();
     CG_C3(CG_SPHERE, 256, 2048, 1u, work + 1);
@@ -1491,9 +1492,9 @@ cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& 
     auto k4 = radius_count4_kernel<CG_CUBE>;
     cudaFuncSetAttribute(k4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
     {
+      const int g4 = resident_grid(k4, W4 * 32, smem4);
       ProfScope prof("radius_count4", st);
-      k4<<<resident_grid(k4, W4 * 32, smem4), W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks,
-                                                                    ids, meta, work, status);
+      k4<<<g4, W4 * 32, smem4, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, ids, meta, work, status);
     }
     note_launch();
     CG_C3(CG_CUBE, 256, 2048, 1u, work + 1);
@@ -1507,8 +1508,9 @@ cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const B
                                 const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
                                 unsigned* work, const uint32_t* status, cudaStream_t st) {
   auto kfn = radius_fill3_kernel<256>;
+  const int g = resident_grid(kfn, 256, 0);
   ProfScope prof("radius_fill3", st);
-  kfn<<<resident_grid(kfn, 256, 0), 256, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, meta, offsets, out, work,
+  kfn<<<g, 256, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, meta, offsets, out, work,
                                                    status);
   note_launch();
   return cudaGetLastError();
