@@ -75,7 +75,7 @@ struct RadiusState {
   // fast kernels: per-group plans, mask / id layouts and the large groups
   struct BlockPlan* plans = nullptr;
   uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
-  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr, *meta = nullptr;
+  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr;
   uint32_t big_n = 0;
   uint32_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
 };
@@ -105,7 +105,7 @@ struct RadiusWork {
   void *scan_scr = nullptr, *plan_scr = nullptr;
   struct BlockPlan* plans = nullptr;
   uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
-  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr, *meta = nullptr;
+  uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr;
   int32_t* row_scratch = nullptr;
   uint32_t cap_nb = 0, cap_m = 0, cap_i = 0;
   uint64_t cap_scr = 0;

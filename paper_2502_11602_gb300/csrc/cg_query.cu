@@ -797,10 +797,8 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       R.mtot = tots[0];
       R.itot = tots[1];
       if (ix->precision == CG_FP32_OFFSET) {
-        R.meta = (uint32_t*)R.bufs.get(16 * (size_t)nb, st);
-        if (!R.meta) return fail(CG_ERR_OOM, "device allocation failed (radius meta)");
-        e = launch_radius_count3(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks, R.ids,
-                                 R.meta, R.ctrs + 14, C.status, st);
+        e = launch_radius_count32(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks, R.ids,
+                                  R.ctrs + 14, C.status, st);
       } else {
         e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
                                  R.masks, R.ids, R.ctrs + 14, C.status, st);
@@ -809,11 +807,11 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
         e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, C.status,
                                    grid, st);
     } else {
-      e = cudaMemsetAsync(R.ctrs + 16, 0, 4, st);
+      e = cudaMemsetAsync(R.ctrs + 16, 0, 8, st);
       if (e == cudaSuccess) {
         if (ix->precision == CG_FP32_OFFSET)
-          e = launch_radius_fill3(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, R.meta, offsets, out,
-                                  R.ctrs + 16, C.status, st);
+          e = launch_radius_fill32(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets, out,
+                                   R.ctrs + 16, C.status, st);
         else
           e = launch_radius_fill2(ix->precision, L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets,
                                   out, R.ctrs + 16, C.status, st);
@@ -908,12 +906,11 @@ cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double
   w.moff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
   w.idoff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
   w.big_list = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_nb, st);
-  w.meta = (uint32_t*)w.bufs.get(16 * (size_t)w.cap_nb, st);
   w.masks = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_m, st);
   w.ids = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_i, st);
   w.row_scratch = (int32_t*)w.bufs.get(4 * (size_t)w.cap_scr, st);
   if (!w.counts || !w.heavy_list || !w.heavy_soff || !w.ctrs || !w.thr || !w.scan_scr || !w.plan_scr || !w.plans ||
-      !w.msize || !w.isize || !w.moff || !w.idoff || !w.big_list || !w.meta || !w.masks || !w.ids || !w.row_scratch)
+      !w.msize || !w.isize || !w.moff || !w.idoff || !w.big_list || !w.masks || !w.ids || !w.row_scratch)
     return fail(CG_ERR_OOM, "device allocation failed (pipeline radius work)");
   return CG_OK;
 }
@@ -958,8 +955,8 @@ cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, 
   if (e != cudaSuccess) return cuda_fail(e, "replay plan");
   replay_check_plan_kernel<<<1, 1, 0, st>>>(w.moff + nb, w.cap_m, w.idoff + nb, w.cap_i, ix->status); note_launch();
   if (ix->precision == CG_FP32_OFFSET)
-    e = launch_radius_count3(kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks, w.ids, w.meta,
-                             w.ctrs + 14, ix->status, st);
+    e = launch_radius_count32(kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks, w.ids,
+                              w.ctrs + 14, ix->status, st);
   else
     e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks,
                              w.ids, w.ctrs + 14, ix->status, st);
@@ -972,8 +969,8 @@ cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, 
   if (e != cudaSuccess) return cuda_fail(e, "replay count");
   replay_check_out_kernel<<<1, 1, 0, st>>>(offsets + n, w.cap_out, H.scratch_total, w.cap_scr, ix->status); note_launch();
   if (ix->precision == CG_FP32_OFFSET)
-    e = launch_radius_fill3(L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, w.meta, offsets, out, w.ctrs + 16,
-                            ix->status, st);
+    e = launch_radius_fill32(L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out, w.ctrs + 16,
+                             ix->status, st);
   else
     e = launch_radius_fill2(ix->precision, L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out,
                             w.ctrs + 16, ix->status, st);

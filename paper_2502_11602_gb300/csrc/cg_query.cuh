@@ -135,17 +135,16 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                 const uint32_t* status, cudaStream_t st);
 
-cudaError_t launch_radius_count3(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
-                                 const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
-                                 uint32_t* counts, uint32_t* masks, uint32_t* ids, uint32_t* meta,
-                                 unsigned* work, uint32_t* status, cudaStream_t st);
-cudaError_t launch_radius_fill3(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
-                                const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
-                                const uint32_t* ids, const uint32_t* meta, const int64_t* offsets, int32_t* out,
-                                unsigned* work, const uint32_t* status, cudaStream_t st);
+// Binary32 records: warp-per-group count and fill for the two size classes.
+cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
+                                  const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
+                                  uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
+                                  uint32_t* status, cudaStream_t st);
+cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
+                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
+                                 const uint32_t* status, cudaStream_t st);
 
-// Builds (or reuses) the plan of an external query set on ix->plan.
-cg_status prepare_queries(cg_index* ix, const double* q, int64_t nq, cudaStream_t st);
 QuerySet query_set(cg_index* ix, const double* q, int64_t nq, bool all_points);
 
 }  // namespace cg
