@@ -66,6 +66,65 @@ void prof_resolve() {
 }
 }  // namespace
 
+namespace {
+struct AuxStreams {
+  int dev = -1;
+  bool ok = false;
+  cudaStream_t s[Fork::kMax - 1] = {};
+  cudaEvent_t fork = nullptr, join[Fork::kMax - 1] = {};
+  ~AuxStreams() { release(); }
+  void release() {
+    if (!ok) return;
+    for (int i = 0; i < Fork::kMax - 1; ++i) {
+      cudaStreamDestroy(s[i]);
+      cudaEventDestroy(join[i]);
+    }
+    cudaEventDestroy(fork);
+    ok = false;
+  }
+  bool ensure() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return false;
+    if (ok && d == dev) return true;
+    release();
+    bool good = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; good && i < Fork::kMax - 1; ++i)
+      good = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+    cudaGetLastError();
+    ok = good;
+    dev = d;
+    return ok;
+  }
+};
+thread_local AuxStreams t_aux;
+}  // namespace
+
+// Without extra streams (creation failed) every branch is the origin itself.
+Fork::Fork(cudaStream_t origin, int branches) : origin_(origin) {
+  for (int i = 0; i < kMax - 1; ++i) aux_[i] = origin;
+  n_ = branches < 1 ? 1 : (branches > kMax ? kMax : branches);
+  if (n_ == 1 || !t_aux.ensure()) {
+    n_ = 1;
+    return;
+  }
+  cudaEventRecord(t_aux.fork, origin);
+  for (int i = 0; i < n_ - 1; ++i) {
+    aux_[i] = t_aux.s[i];
+    join_[i] = t_aux.join[i];
+    cudaStreamWaitEvent(aux_[i], t_aux.fork, 0);
+  }
+}
+
+void Fork::join() {
+  if (joined_) return;
+  joined_ = true;
+  for (int i = 0; i < n_ - 1; ++i) {
+    cudaEventRecord(join_[i], aux_[i]);
+    cudaStreamWaitEvent(origin_, join_[i], 0);
+  }
+}
+
 ProfScope::ProfScope(const char* nm, cudaStream_t s) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

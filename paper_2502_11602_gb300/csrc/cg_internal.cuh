@@ -58,6 +58,28 @@ void note_launch(int n = 1);
 // cg_profile_enable): a scope records CUDA events around the launches it
 // encloses on their stream; nothing is recorded while a stream is being
 // captured into a graph.
+// Fork / join of independent kernels of one pass onto extra streams (one
+// set per host thread and device), so that they overlap on the GPU: every
+// branch starts after the work already on the origin stream, and the origin
+// continues only after every branch.  Works inside a stream capture (the
+// branches become parallel graph nodes).
+struct Fork {
+  static constexpr int kMax = 4;
+  Fork(cudaStream_t origin, int branches);
+  cudaStream_t operator[](int i) const { return i == 0 ? origin_ : aux_[i - 1]; }
+  void join();
+  ~Fork() { join(); }
+  Fork(const Fork&) = delete;
+  Fork& operator=(const Fork&) = delete;
+
+ private:
+  cudaStream_t origin_;
+  cudaStream_t aux_[kMax - 1];
+  cudaEvent_t join_[kMax - 1];
+  int n_ = 1;
+  bool joined_ = false;
+};
+
 struct ProfScope {
   ProfScope(const char* name, cudaStream_t st);
   ~ProfScope();

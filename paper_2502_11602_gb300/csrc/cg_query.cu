@@ -796,29 +796,39 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       R.big_n = tots[2];
       R.mtot = tots[0];
       R.itot = tots[1];
-      if (ix->precision == CG_FP32_OFFSET) {
-        e = launch_radius_count32(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks, R.ids,
-                                  R.ctrs + 14, C.status, st);
-      } else {
-        e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
-                                 R.masks, R.ids, R.ctrs + 14, C.status, st);
+      {
+        // the size classes and the general kernel's groups are disjoint: they
+        // run concurrently, so that each fills the others' tails
+        ProfScope prof("radius_count_kernels", st);
+        Fork f(st, 4);
+        const cudaStream_t sts[3] = {f[0], f[1], f[2]};
+        if (ix->precision == CG_FP32_OFFSET) {
+          e = launch_radius_count32(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks,
+                                    R.ids, R.ctrs + 20, C.status, sts);
+        } else {
+          e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
+                                   R.masks, R.ids, R.ctrs + 14, C.status, f[0]);
+        }
+        if (e == cudaSuccess && R.big_n > 0)
+          e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, C.status,
+                                     grid, f[3]);
       }
-      if (e == cudaSuccess && R.big_n > 0)
-        e = dispatch_radius<false>(ix->precision, kernel, Lbig, R.counts, nullptr, nullptr, H, work, C.status,
-                                   grid, st);
     } else {
-      e = cudaMemsetAsync(R.ctrs + 16, 0, 8, st);
+      e = cudaMemsetAsync(R.ctrs + 16, 0, 48, st);  // fill counters (binary64: 16, binary32: 24..26)
       if (e == cudaSuccess) {
+        ProfScope prof("radius_fill_kernels", st);
+        Fork f(st, 4);
+        const cudaStream_t sts[3] = {f[0], f[1], f[2]};
         if (ix->precision == CG_FP32_OFFSET)
           e = launch_radius_fill32(L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets, out,
-                                   R.ctrs + 16, C.status, st);
+                                   R.ctrs + 24, C.status, sts);
         else
           e = launch_radius_fill2(ix->precision, L.iv, L.qs, R.plans, R.moff, R.idoff, R.masks, R.ids, offsets,
-                                  out, R.ctrs + 16, C.status, st);
+                                  out, R.ctrs + 16, C.status, f[0]);
+        if (e == cudaSuccess && R.big_n > 0)
+          e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, C.status, grid,
+                                    f[3]);
       }
-      if (e == cudaSuccess && R.big_n > 0)
-        e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, work, C.status, grid,
-                                  st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "radius kernel");
   }
@@ -954,29 +964,37 @@ cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, 
   if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.isize, w.idoff, nb, w.plan_scr, ix->status, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay plan");
   replay_check_plan_kernel<<<1, 1, 0, st>>>(w.moff + nb, w.cap_m, w.idoff + nb, w.cap_i, ix->status); note_launch();
-  if (ix->precision == CG_FP32_OFFSET)
-    e = launch_radius_count32(kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks, w.ids,
-                              w.ctrs + 14, ix->status, st);
-  else
-    e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks,
-                             w.ids, w.ctrs + 14, ix->status, st);
-  // groups too large for the fast kernels: the list length is read on the
-  // device, an empty list costs one pass over the grid
-  if (e == cudaSuccess)
-    e = dispatch_radius<false>(ix->precision, kernel, Lbig, w.counts, nullptr, nullptr, H, w.ctrs + 6, ix->status,
-                               grid, st);
+  {
+    Fork f(st, 4);
+    const cudaStream_t sts[3] = {f[0], f[1], f[2]};
+    if (ix->precision == CG_FP32_OFFSET)
+      e = launch_radius_count32(kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts, w.masks, w.ids,
+                                w.ctrs + 20, ix->status, sts);
+    else
+      e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.moff, w.idoff, w.counts,
+                               w.masks, w.ids, w.ctrs + 14, ix->status, f[0]);
+    // groups too large for the fast kernels: the list length is read on the
+    // device, an empty list costs one pass over the grid
+    if (e == cudaSuccess)
+      e = dispatch_radius<false>(ix->precision, kernel, Lbig, w.counts, nullptr, nullptr, H, w.ctrs + 6,
+                                 ix->status, grid, f[3]);
+  }
   if (e == cudaSuccess) e = exclusive_scan_u32_i64(w.counts, offsets, n, w.scan_scr, ix->status, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay count");
   replay_check_out_kernel<<<1, 1, 0, st>>>(offsets + n, w.cap_out, H.scratch_total, w.cap_scr, ix->status); note_launch();
-  if (ix->precision == CG_FP32_OFFSET)
-    e = launch_radius_fill32(L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out, w.ctrs + 16,
-                             ix->status, st);
-  else
-    e = launch_radius_fill2(ix->precision, L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out,
-                            w.ctrs + 16, ix->status, st);
-  if (e == cudaSuccess)
-    e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, w.ctrs + 8, ix->status, grid,
-                              st);
+  {
+    Fork f(st, 4);
+    const cudaStream_t sts[3] = {f[0], f[1], f[2]};
+    if (ix->precision == CG_FP32_OFFSET)
+      e = launch_radius_fill32(L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out, w.ctrs + 24,
+                               ix->status, sts);
+    else
+      e = launch_radius_fill2(ix->precision, L.iv, L.qs, w.plans, w.moff, w.idoff, w.masks, w.ids, offsets, out,
+                              w.ctrs + 16, ix->status, f[0]);
+    if (e == cudaSuccess)
+      e = dispatch_radius<true>(ix->precision, kernel, Lbig, nullptr, offsets, out, H, w.ctrs + 8, ix->status,
+                                grid, f[3]);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "replay fill");
   row_sort_kernel<<<152 * 4, 512, 4 * kSmemSortCap, st>>>(w.heavy_list, w.heavy_soff, w.ctrs + 0, H.cap, offsets, out,
                                                          w.row_scratch, ix->status); note_launch();

@@ -139,11 +139,11 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                   const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
-                                  uint32_t* status, cudaStream_t st);
+                                  uint32_t* status, const cudaStream_t* sts);
 cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                  const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
-                                 const uint32_t* status, cudaStream_t st);
+                                 const uint32_t* status, const cudaStream_t* sts);
 
 QuerySet query_set(cg_index* ix, const double* q, int64_t nq, bool all_points);
 

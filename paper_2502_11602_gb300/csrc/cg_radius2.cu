@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
       P->nsp = (uint16_t)(big ? 0 : nsp);
       P->W = (uint16_t)W;
       P->heavy = big ? 1u : 0u;
-      P->pad_[0] = (PREC == 1 && K > 1024u) ? 1u : 0u;  // size class for the binary32 kernels
+      // size class of the binary32 kernels: K <= 512, <= 1024, <= 2048
+      P->pad_[0] = PREC == 1 ? (K > 1024u ? 2u : (K > 512u ? 1u : 0u)) : 0u;
       // one hit mask per (32-candidate word, query)
       msize[b] = big ? 0u : nq * W;
       isize[b] = big ? 0u : K;
@@ -539,7 +540,7 @@ struct C5 {
   static constexpr size_t PH1 = 4 * (size_t)KC + 4 * (size_t)NBK + 2 * (size_t)KC;  // ids, buckets, order
   static constexpr size_t R1 = ((PH2 > PH1 ? PH2 : PH1) + 15) / 16 * 16;
   static constexpr size_t SLOT = 2 * (size_t)KC;                                    // id-order slot of each candidate
-  static constexpr size_t RUNS = 4 * 2 * 36;
+  static constexpr size_t RUNS = 4 * (2 * 36 + 32);
   static constexpr size_t per_warp = (R1 + SLOT + RUNS + 15) / 16 * 16;
 };
 
@@ -582,6 +583,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   uint16_t* slot_of = reinterpret_cast<uint16_t*>(base + L::R1);  // run position -> id order
   uint32_t* rstart = reinterpret_cast<uint32_t*>(base + L::R1 + L::SLOT);
   uint32_t* roff = rstart + 36;
+  uint32_t* qcnt = roff + 36;  // [32] hits of the current 32 queries
   const unsigned lane = threadIdx.x & 31u;
   const Thresholds thr = *thr_p;
   const float4* __restrict__ pts = ix.pts32;
@@ -733,14 +735,15 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       z[h] = far;
     }
     __syncwarp();
-    // 4. tests: lanes = (query, slice of words)
+    // 4. tests: lanes = (query, slice of words); Sl lanes share a query
     for (uint32_t qg0 = 0; qg0 < nq; qg0 += 32) {
       const uint32_t nqg = min(32u, nq - qg0);
-      uint32_t Sl = 1;
-      while (Sl * 2 <= 32u / nqg && Sl * 2 <= Wp) Sl *= 2;
-      const uint32_t qi = lane / Sl, s = lane % Sl;
+      const uint32_t Sl = min(Wp, 32u / nqg);
+      const uint32_t qi = lane / Sl, s = lane - qi * Sl;
       const bool active = qi < nqg;
       uint32_t cnt = 0, qid = 0;
+      qcnt[lane] = 0u;
+      __syncwarp();
       if (active) {
         const uint32_t q = qg0 + qi;
         const float4 qq = qsrc[q0 + q];
@@ -778,22 +781,27 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
           cnt += __popc(m_in);
         }
       }
-      for (uint32_t o = 1; o < Sl; o <<= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-      if (active && s == 0) counts[qid] = cnt;
+      if (active) atomicAdd(&qcnt[qi], cnt);
+      __syncwarp();
+      if (active && s == 0) counts[qid] = qcnt[qi];
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
 // Fill of the binary32 groups: the group's sorted ids to shared memory, then
 // per chunk of 32 queries their masks (word-major, one coalesced row per
-// word); per query, lanes = words: popcounts and a warp scan place each
-// word's hits, the bits are expanded (ascending ids) into a staging row that
-// the warp writes out with coalesced stores.
+// word).  Rows are expanded in lane segments of seg = 2^ceil(log2 Wp) lanes,
+// 32 / seg rows at a time (one word per lane): a segmented scan of the
+// words' popcounts places each word's hits, the bits are expanded (ascending
+// ids) into the segment's staging row, and the segment writes its row out
+// with coalesced stores.  Groups of more than 32 words use the whole warp
+// per row, two words per lane.
 template <int KC>
 struct F5 {
   static constexpr int WMAX = KC / 32;
-  static constexpr size_t per_warp = 4 * (size_t)KC + 4 * (size_t)WMAX * 33 + 4 * (size_t)KC + 8 * 32;
+  static constexpr int ROW = KC > 1024 ? KC : 1024;  // staging entries
+  static constexpr size_t per_warp = 4 * (size_t)KC + 4 * (size_t)WMAX * 33 + 4 * (size_t)ROW + 8 * 32;
 };
 
 template <int KC, int NWARP>
@@ -810,10 +818,10 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
   using L = F5<KC>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * L::per_warp;
-  uint32_t* sids = reinterpret_cast<uint32_t*>(base);  // [KC]
-  uint32_t* ms = sids + KC;                             // [WMAX][33]
-  int32_t* row = reinterpret_cast<int32_t*>(ms + L::WMAX * 33);  // [KC]
-  long long* soff = reinterpret_cast<long long*>(row + KC);     // [32]
+  uint32_t* sids = reinterpret_cast<uint32_t*>(base);             // [KC]
+  uint32_t* ms = sids + KC;                                        // [WMAX][33]
+  int32_t* row = reinterpret_cast<int32_t*>(ms + L::WMAX * 33);   // [ROW]
+  long long* soff = reinterpret_cast<long long*>(row + L::ROW);  // [32]
   const unsigned lane = threadIdx.x & 31u;
   const float4* __restrict__ qsrc = qs.all_points ? ix.pts32 : qs.qrec;
   for (;;) {
@@ -829,6 +837,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
     const uint32_t io = idoff[b];
     const uint32_t* __restrict__ mb = masks + moff[b];
     for (uint32_t j = lane; j < K; j += 32) sids[j] = __ldg(ids + io + j);
+    uint32_t seg = 1;
+    while (seg < Wp && seg < 32) seg <<= 1;
     for (uint32_t c0 = 0; c0 < nq; c0 += 32) {
       const uint32_t nc = min(32u, nq - c0);
       __syncwarp();
@@ -837,31 +847,60 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
         for (uint32_t w = 0; w < Wp; ++w) ms[w * 33 + lane] = __ldg(mb + w * nq + c0 + lane);
       }
       __syncwarp();
-      for (uint32_t t = 0; t < nc; ++t) {
-        // words 0..31 (lane = word), then words 32..63 after all of them
-        uint32_t tot = 0;
-#pragma unroll
-        for (int half = 0; half < (L::WMAX > 32 ? 2 : 1); ++half) {
-          const uint32_t w = lane + 32u * half;
-          uint32_t m = w < Wp ? ms[w * 33 + t] : 0u;
+      if (L::WMAX <= 32 || Wp <= 32) {
+        const uint32_t rows = 32u / seg, j = lane / seg, wl = lane % seg;
+        int32_t* srow = row + j * seg * 32u;
+        for (uint32_t t0 = 0; t0 < nc; t0 += rows) {
+          const uint32_t t = t0 + j;
+          const bool live = t < nc;
+          uint32_t m = (live && wl < Wp) ? ms[wl * 33 + t] : 0u;
           const uint32_t c = __popc(m);
           uint32_t incl = c;
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (unsigned)o) incl += y;
+          for (uint32_t o = 1; o < seg; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o, seg);
+            if (wl >= o) incl += y;
           }
-          uint32_t p = tot + incl - c;
-          tot += __shfl_sync(0xffffffffu, incl, 31);
+          const uint32_t tot = __shfl_sync(0xffffffffu, incl, seg - 1, seg);
+          uint32_t p = incl - c;
           while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
-            row[p++] = (int32_t)sids[w * 32 + bit];
+            srow[p++] = (int32_t)sids[wl * 32 + bit];
           }
+          __syncwarp();
+          if (live) {
+            int32_t* dst = out + soff[t];
+            for (uint32_t i = wl; i < tot; i += seg) dst[i] = srow[i];
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        int32_t* dst = out + soff[t];
-        for (uint32_t i = lane; i < tot; i += 32) dst[i] = row[i];
-        __syncwarp();
+      } else {
+        for (uint32_t t = 0; t < nc; ++t) {
+          // words 0..31 (lane = word), then words 32..63 after all of them
+          uint32_t tot = 0;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            const uint32_t w = lane + 32u * half;
+            uint32_t m = w < Wp ? ms[w * 33 + t] : 0u;
+            const uint32_t c = __popc(m);
+            uint32_t incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= (unsigned)o) incl += y;
+            }
+            uint32_t p = tot + incl - c;
+            tot += __shfl_sync(0xffffffffu, incl, 31);
+            while (m) {
+              const int bit = __ffs(m) - 1;
+              m &= m - 1;
+              row[p++] = (int32_t)sids[w * 32 + bit];
+            }
+          }
+          __syncwarp();
+          int32_t* dst = out + soff[t];
+          for (uint32_t i = lane; i < tot; i += 32) dst[i] = row[i];
+          __syncwarp();
+        }
       }
     }
   }
@@ -1036,25 +1075,29 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                   const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
-                                  uint32_t* status, cudaStream_t st) {
-  // size class 0: K <= 1024 (4 warps per CTA); class 1: 1024 < K <= 2048 (2 warps)
+                                  uint32_t* status, const cudaStream_t* sts) {
+  // size classes: K <= 512 and <= 1024 (4 warps per CTA), <= 2048 (2 warps);
+  // work[0..2] are their group counters, sts[0..2] their streams
 #define CG_C5(KN, KC, NW, CLS, WORK)                                                             \
   do {                                                                                            \
     auto kfn = radius_count5_kernel<KN, KC, NW>;                                                 \
     const size_t smem = C5<KC>::per_warp * NW;                                                   \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
-    ProfScope prof(CLS ? "radius_count5_2k" : "radius_count5_1k", st);                           \
+    cudaStream_t st = sts[CLS];                                                                  \
+    ProfScope prof(CLS == 2 ? "radius_count5_2k" : (CLS ? "radius_count5_1k" : "radius_count5_512"), st); \
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, ids, WORK, status, \
                                   CLS);                                                           \
     note_launch();                                                                                \
   } while (0)
   if (kern == CG_SPHERE) {
-    CG_C5(CG_SPHERE, 1024, 4, 0u, work);
-    CG_C5(CG_SPHERE, 2048, 2, 1u, work + 1);
+    CG_C5(CG_SPHERE, 512, 4, 0u, work);
+    CG_C5(CG_SPHERE, 1024, 4, 1u, work + 1);
+    CG_C5(CG_SPHERE, 2048, 2, 2u, work + 2);
   } else {
-    CG_C5(CG_CUBE, 1024, 4, 0u, work);
-    CG_C5(CG_CUBE, 2048, 2, 1u, work + 1);
+    CG_C5(CG_CUBE, 512, 4, 0u, work);
+    CG_C5(CG_CUBE, 1024, 4, 1u, work + 1);
+    CG_C5(CG_CUBE, 2048, 2, 2u, work + 2);
   }
 #undef CG_C5
   return cudaGetLastError();
@@ -1063,19 +1106,21 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
 cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                  const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
-                                 const uint32_t* status, cudaStream_t st) {
+                                 const uint32_t* status, const cudaStream_t* sts) {
 #define CG_F5(KC, NW, CLS, WORK)                                                                  \
   do {                                                                                            \
     auto kfn = radius_fill5_kernel<KC, NW>;                                                      \
     const size_t smem = F5<KC>::per_warp * NW;                                                   \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
-    ProfScope prof(CLS ? "radius_fill5_2k" : "radius_fill5_1k", st);                             \
+    cudaStream_t st = sts[CLS];                                                                  \
+    ProfScope prof(CLS == 2 ? "radius_fill5_2k" : (CLS ? "radius_fill5_1k" : "radius_fill5_512"), st); \
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, WORK, status, CLS); \
     note_launch();                                                                                \
   } while (0)
-  CG_F5(1024, 4, 0u, work);
-  CG_F5(2048, 2, 1u, work + 1);
+  CG_F5(512, 4, 0u, work);
+  CG_F5(1024, 4, 1u, work + 1);
+  CG_F5(2048, 2, 2u, work + 2);
 #undef CG_F5
   return cudaGetLastError();
 }
