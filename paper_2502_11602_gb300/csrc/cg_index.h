@@ -115,7 +115,8 @@ struct RadiusWork {
 // Workspace of a replayed k-NN pass.
 struct KnnWork {
   DevBufs bufs;
-  uint32_t *slow = nullptr, *ctrs = nullptr;
+  uint32_t *slow = nullptr, *ctrs = nullptr, *bslot = nullptr;
+  float* br2 = nullptr;
   Thresholds* thr = nullptr;
 };
 

@@ -77,6 +77,22 @@ struct KBound {
   }
 };
 
+// The band of a precision: alpha = per-axis bound on the binary32 difference
+// error (pad_[0] of the k-NN thresholds), beta = relative rounding of the
+// squares and sums; zero width for binary64 records (their screen value is
+// the exact one rounded up).
+template <int PREC>
+__device__ __forceinline__ KBound make_kbound(const Thresholds& thr) {
+  KBound kb;
+  const double u = 5.9604644775390625e-08, U = 1.1102230246251565e-16;
+  const double alpha = PREC == 1 ? (double)thr.pad_[0] * (1.0 + u) : 0.0;
+  const double beta = PREC == 1 ? (u + U) * (1.0 + 2.0 * U) : 0.0;
+  kb.c1 = (float)(2.0 * alpha * (1.0 + beta) * 1.7320508075688774);
+  kb.c0 = (float)(3.0 * alpha * alpha);
+  kb.c2 = PREC == 1 ? (float)(2.0 * beta + beta * beta + 3.0000002 * u + 4.0 * U) : 1.2e-7f;
+  return kb;
+}
+
 __device__ __forceinline__ float rec_u_k(const float4& q, const Tile& T, int a) {
   float x = a == 0 ? q.x : (a == 1 ? q.y : q.z);
   return __fmul_rn(__fadd_rn(x, T.D[a]), T.inv_sf[a]);
@@ -141,15 +157,7 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
   __shared__ uint32_t s_blk;
 
   const Thresholds thr = *thr_p;
-  KBound kb;
-  {
-    const double u = 5.9604644775390625e-08, U = 1.1102230246251565e-16;
-    const double alpha = PREC == 1 ? (double)thr.pad_[0] * (1.0 + u) : 0.0;
-    const double beta = PREC == 1 ? (u + U) * (1.0 + 2.0 * U) : 0.0;
-    kb.c1 = (float)(2.0 * alpha * (1.0 + beta) * 1.7320508075688774);
-    kb.c0 = (float)(3.0 * alpha * alpha);
-    kb.c2 = PREC == 1 ? (float)(2.0 * beta + beta * beta + 3.0000002 * u + 4.0 * U) : 1.2e-7f;
-  }
+  const KBound kb = make_kbound<PREC>(thr);
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32) : reinterpret_cast<const R*>(ix.pts64s);
   const R* __restrict__ qsrc = qs.all_points ? pts
@@ -317,6 +325,442 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
       }
       __syncthreads();
     }
+  }
+}
+
+// ------------------------------------------------ fast path, binary32 records
+
+// One warp per voxel group, lanes = queries.  The group's box (RB voxels
+// around its voxel on each indexed axis) is staged in shared memory, its
+// candidates bucketed by their distance D from the group voxel's centre
+// (64 buckets, bucket u holds D in [u bw, (u+1) bw)).  Each lane keeps the
+// L = k + spare smallest binary32 values of its query in registers (sorted);
+// candidates below a lane's current L-th value are queued (8 per lane) and
+// merged into the lists whenever a queue fills, so the warp pays for the
+// insertions of its busiest lane, not for every lane's.  Before each bucket,
+// |p - q| >= D - |q - c| >= u bw - |q - c| bounds every later candidate:
+// once that exceeds a lane's L-th value nothing later can enter its list, and
+// when it holds for every lane the warp stops scanning.  Then, per lane: the
+// certified band (every candidate within twice the error bound of the k-th
+// value is in the list, as the list keeps every candidate below its L-th
+// value, which must lie beyond that band), binary64 values of the band,
+// order (d2, id), and the stop test against the box wall.
+// A query the box cannot decide (its k-th may lie outside the box) goes to
+// the bounded search with the box's exact k-th value as an upper bound of
+// the true one; groups too large to stage go to the ring-by-ring path.
+constexpr int K5_NB = 64;
+constexpr int K5_Q = 8;  // queued candidates per lane
+
+template <int KC>
+struct K5Smem {
+  static constexpr size_t per_warp = 16 * (size_t)KC + (size_t)KC + 4 * (2 * K5_NB + 2) + 4 * 2 * 12 +
+                                     8 * (size_t)K5_Q * 32;
+  static constexpr size_t per_warp_aligned = (per_warp + 15) / 16 * 16;
+};
+
+// wall2_lower for one box given by scalars (no array whose address is taken)
+__device__ __forceinline__ float wall2_box(const float4& q, const Tile& T, int dim, int lo0, int lo1, int lo2, int hi0,
+                                          int hi1, int hi2, float e_q) {
+  float w = INFINITY;
+  const float qa[3] = {q.x, q.y, q.z};
+  const int lov[3] = {lo0, lo1, lo2}, hiv[3] = {hi0, hi1, hi2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      const float u = __fmul_rn(__fadd_rn(qa[a], T.D[a]), T.inv_sf[a]);
+      const float eta = T.eta + (fabsf(u) + fabsf(qa[a]) * T.inv_sf[a]) * 3.0e-7f + e_q * T.inv_sf[a];
+      if (lov[a] > 0) w = fminf(w, (u - (float)lov[a] - eta) * (float)T.s[a]);
+      if (hiv[a] < T.n[a] - 1) w = fminf(w, ((float)(hiv[a] + 1) - u - eta) * (float)T.s[a]);
+    }
+  }
+  if (w == INFINITY) return INFINITY;
+  if (w <= 0.f) return 0.f;
+  return __fmul_rd(__fmul_rd(w, w), 0.99999f);
+}
+
+__device__ __forceinline__ float centre_dist(const float4& r, float cx, float cy, float cz, float zw) {
+  const float dx = r.x - cx, dy = r.y - cy, dz = (r.z - cz) * zw;
+  return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+template <int L>
+__device__ __forceinline__ void topl_insert(float (&v)[L], uint32_t (&id)[L], float d, uint32_t j) {
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const bool p = d < v[i];
+    const float tv = v[i];
+    const uint32_t ti = id[i];
+    v[i] = p ? d : tv;
+    id[i] = p ? j : ti;
+    d = p ? tv : d;
+    j = p ? ti : j;
+  }
+}
+
+template <int KC, int L, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet qs, const Thresholds* __restrict__ thr_p,
+                                                          int k, int32_t* __restrict__ out_idx,
+                                                          double* __restrict__ out_d2, uint32_t* __restrict__ slow_list,
+                                                          uint32_t* slow_cnt, uint32_t* __restrict__ bslot,
+                                                          float* __restrict__ br2, uint32_t* bcnt, unsigned* work,
+                                                          uint32_t* status, uint32_t kcls) {
+  if (replan_pending(status)) return;  // the later kernels then find empty lists
+  constexpr int RB = 1;
+  using S = K5Smem<KC>;
+  extern __shared__ __align__(32) unsigned char smem[];
+  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * S::per_warp_aligned;
+  float4* recs = reinterpret_cast<float4*>(base);                 // [KC] in bucket order
+  uint8_t* bkt = reinterpret_cast<uint8_t*>(recs + KC);           // [KC] bucket of each span-order candidate
+  uint32_t* bstart = reinterpret_cast<uint32_t*>(bkt + KC);       // [NB + 1]
+  uint32_t* cursor = bstart + K5_NB + 1;                          // [NB + 1]
+  uint32_t* sp_start = cursor + K5_NB + 1;                        // [12]
+  uint32_t* sp_off = sp_start + 12;                               // [12]
+  float* qd = reinterpret_cast<float*>(sp_off + 12);              // [Q][32] queued values
+  uint32_t* qj = reinterpret_cast<uint32_t*>(qd + K5_Q * 32);     // [Q][32] queued slots
+  const unsigned lane = threadIdx.x & 31u;
+  const Thresholds thr = *thr_p;
+  const KBound kb = make_kbound<1>(thr);
+  const float4* __restrict__ pts = ix.pts32;
+  const float4* __restrict__ qsrc = qs.all_points ? pts : qs.qrec;
+  const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
+  const int dim = ix.dim;
+  for (;;) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(work, 1u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= qs_nblocks(qs)) break;
+    const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
+    const uint32_t bkey = qs.blk_key[b];
+    const Tile& T = ix.tiles[ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey)];
+    const uint32_t g = bkey - T.key_base;
+    int c0, c1, c2 = 0;
+    if (dim == 2) { c0 = (int)(g / (uint32_t)T.n[1]); c1 = (int)(g % (uint32_t)T.n[1]); }
+    else { c2 = (int)(g % (uint32_t)T.n[2]); const uint32_t ij = g / (uint32_t)T.n[2]; c0 = (int)(ij / (uint32_t)T.n[1]); c1 = (int)(ij % (uint32_t)T.n[1]); }
+    const int lo0 = max(c0 - RB, 0), hi0 = min(c0 + RB, T.n[0] - 1);
+    const int lo1 = max(c1 - RB, 0), hi1 = min(c1 + RB, T.n[1] - 1);
+    const int lo2 = dim == 3 ? max(c2 - RB, 0) : 0, hi2 = dim == 3 ? min(c2 + RB, T.n[2] - 1) : T.n[2] - 1;
+    const bool exhausted = lo0 == 0 && hi0 == T.n[0] - 1 && lo1 == 0 && hi1 == T.n[1] - 1 &&
+                           (dim == 2 || (lo2 == 0 && hi2 == T.n[2] - 1));
+    const int ni = hi0 - lo0 + 1, nj = hi1 - lo1 + 1;
+    const int nsp = dim == 2 ? ni : ni * nj;  // <= NSP
+    // spans (one contiguous run of sorted points per grid row / column)
+    uint32_t len = 0, st0 = 0;
+    if ((int)lane < nsp) {
+      uint32_t k0, k1;
+      if (dim == 2) {
+        const uint32_t row = (uint32_t)(lo0 + (int)lane) * (uint32_t)T.n[1];
+        k0 = T.key_base + row + (uint32_t)lo1;
+        k1 = T.key_base + row + (uint32_t)hi1;
+      } else {
+        const int i = lo0 + (int)lane / nj, j = lo1 + (int)lane % nj;
+        const uint32_t col = ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) * (uint32_t)T.n[2];
+        k0 = T.key_base + col + (uint32_t)lo2;
+        k1 = T.key_base + col + (uint32_t)hi2;
+      }
+      const uint2 sp = row_span(ix, T, k0, k1);
+      st0 = sp.x;
+      len = sp.y - sp.x;
+    }
+    uint32_t incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
+    }
+    const uint32_t K = __shfl_sync(0xffffffffu, incl, 31);
+    // size classes: 0: K <= 512, 1: K <= 1024, 2: K <= 2048 (and the groups too large to stage)
+    if (kcls == 0 ? K > 512u : (kcls == 1 ? (K <= 512u || K > 1024u) : K <= 1024u)) continue;
+    if (K > (uint32_t)KC) {  // too large to stage: the ring-by-ring path
+      for (uint32_t t = qb0 + lane; t < qb1; t += 32) slow_list[atomicAdd(slow_cnt, 1u)] = __float_as_uint(qsrc[t].w);
+      continue;
+    }
+    if ((int)lane < nsp) { sp_start[lane] = st0; sp_off[lane] = incl - len; }
+    // the group voxel's centre in offset coordinates and the bucket width
+    const float cx = __fsub_rn(__fmul_rn((float)c0 + 0.5f, (float)T.s[0]), T.D[0]);
+    const float cy = __fsub_rn(__fmul_rn((float)c1 + 0.5f, (float)T.s[1]), T.D[1]);
+    const float cz = dim == 3 ? __fsub_rn(__fmul_rn((float)c2 + 0.5f, (float)T.s[2]), T.D[2]) : 0.f;
+    const float zw = dim == 3 ? 1.f : 0.f;  // z counts in the centre distance of 3D grids only
+    const float smax = fmaxf(fmaxf((float)T.s[0], (float)T.s[1]), dim == 3 ? (float)T.s[2] : 0.f);
+    const float bw = (dim == 2 ? 1.42f : 1.74f) * ((float)RB + 0.5f) * smax / (float)K5_NB;
+    const float inv_bw = 1.0f / bw;
+    for (int u = (int)lane; u <= K5_NB; u += 32) bstart[u] = 0u;
+    __syncwarp();
+    // bucket counts, then starts, then the records in bucket order
+    for (int r = 0; r < nsp; ++r) {
+      const uint32_t o = sp_off[r], l = (r + 1 < nsp ? sp_off[r + 1] : K) - o, s0 = sp_start[r];
+      for (uint32_t t = lane; t < l; t += 32) {
+        const float4 r4 = __ldg(pts + s0 + t);
+        const int u = min(K5_NB - 1, (int)(centre_dist(r4, cx, cy, cz, zw) * inv_bw));
+        bkt[o + t] = (uint8_t)u;
+        atomicAdd(&bstart[u], 1u);
+      }
+    }
+    __syncwarp();
+    {
+      const uint32_t a0 = bstart[2 * lane], a1 = bstart[2 * lane + 1];
+      uint32_t inc2 = a0 + a1;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc2, o);
+        if (lane >= (unsigned)o) inc2 += y;
+      }
+      const uint32_t ex = inc2 - a0 - a1;
+      __syncwarp();
+      bstart[2 * lane] = ex;
+      bstart[2 * lane + 1] = ex + a0;
+      cursor[2 * lane] = ex;
+      cursor[2 * lane + 1] = ex + a0;
+      if (lane == 31) bstart[K5_NB] = K;
+    }
+    __syncwarp();
+    for (int r = 0; r < nsp; ++r) {
+      const uint32_t o = sp_off[r], l = (r + 1 < nsp ? sp_off[r + 1] : K) - o, s0 = sp_start[r];
+      for (uint32_t t = lane; t < l; t += 32) recs[atomicAdd(&cursor[bkt[o + t]], 1u)] = __ldg(pts + s0 + t);
+    }
+    __syncwarp();
+    // queries, one per lane
+    for (uint32_t qc = qb0; qc < qb1; qc += 32) {
+      __syncwarp();
+      const bool live = qc + lane < qb1;
+      const float4 q = live ? qsrc[qc + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const uint32_t qid = __float_as_uint(q.w);
+      const float rq = centre_dist(q, cx, cy, cz, zw);
+      float v[L];
+      uint32_t id[L];
+#pragma unroll
+      for (int i = 0; i < L; ++i) { v[i] = INFINITY; id[i] = 0xffffffffu; }
+      float gate = INFINITY;  // the L-th value at the last merge
+      uint32_t nqd = 0;       // queued candidates of this lane
+      for (int u = 0; u < K5_NB; ++u) {
+        const uint32_t s0 = bstart[u], s1 = bstart[u + 1];
+        if (s0 == s1) continue;
+        // later candidates p have |p - q| >= t, so d2(p) >= t^2 and their
+        // binary32 value is at least t^2 - B(t^2) (B grows slower than d2)
+        const float t = __fsub_rd(__fsub_rd((float)u * bw, rq), 1e-3f * bw + 1e-5f);
+        const float t2 = __fmul_rd(t, t);
+        const bool done = !live || (t > 0.f && __fsub_rd(t2, kb.at(t2)) > gate);
+        if (__all_sync(0xffffffffu, done)) break;
+        for (uint32_t j = s0; j < s1; j += 2) {  // two candidates per step
+          const bool two = j + 1 < s1;
+          const float4 p = recs[j];
+          const float4 p1 = recs[two ? j + 1 : j];
+          const float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
+          const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const float ex1 = __fsub_rn(p1.x, q.x), ey1 = __fsub_rn(p1.y, q.y), ez1 = __fsub_rn(p1.z, q.z);
+          const float d1 = __fmaf_rn(ez1, ez1, __fmaf_rn(ey1, ey1, __fmul_rn(ex1, ex1)));
+          if (live && d < gate) {
+            qd[nqd * 32 + lane] = d;
+            qj[nqd * 32 + lane] = j;
+            ++nqd;
+          }
+          if (live && two && d1 < gate) {
+            qd[nqd * 32 + lane] = d1;
+            qj[nqd * 32 + lane] = j + 1;
+            ++nqd;
+          }
+          if (__any_sync(0xffffffffu, nqd >= (uint32_t)K5_Q - 1u)) {  // merge the queues
+            for (uint32_t e = 0; e < nqd; ++e) {
+              const float de = qd[e * 32 + lane];
+              if (de < v[L - 1]) topl_insert<L>(v, id, de, qj[e * 32 + lane]);
+            }
+            nqd = 0;
+            gate = v[L - 1];
+          }
+        }
+      }
+      for (uint32_t e = 0; e < nqd; ++e) {
+        const float de = qd[e * 32 + lane];
+        if (de < v[L - 1]) topl_insert<L>(v, id, de, qj[e * 32 + lane]);
+      }
+      if (!live) continue;
+      // found: candidates in the list (all of the box when it holds fewer than L)
+      int found = 0;
+#pragma unroll
+      for (int i = 0; i < L; ++i) found += v[i] < INFINITY ? 1 : 0;
+      const int kk = min(k, found);
+      bool undecided = false;
+      float W2 = INFINITY;
+      if (!exhausted) {
+        W2 = wall2_box(q, T, dim, lo0, lo1, lo2, hi0, hi1, hi2, thr.e_q);
+        undecided = !(W2 > 0.f) || found < k;
+      }
+      // the certified band: every candidate within 2 B of the k-th value
+      int m = 0;
+      if (!undecided && kk > 0) {
+        float tau = 0.f;  // v is ascending: the k-th value is the largest of the first kk
+#pragma unroll
+        for (int i = 0; i < L; ++i) tau = fmaxf(tau, i < kk ? v[i] : 0.f);
+        const float cut = __fadd_ru(tau, 2.0f * kb.at(tau));
+#pragma unroll
+        for (int i = 0; i < L; ++i) m += v[i] <= cut ? 1 : 0;
+        if (m == L && v[L - 1] < INFINITY) undecided = true;  // the band may continue past the list
+      }
+      double ex[L];
+      uint32_t cid[L];
+      double kth = INFINITY;
+      if (!undecided) {
+        kth = 0.0;
+        // binary64 values of the band, order (d2, id)
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+          if (i < m) {
+            cid[i] = __float_as_uint(recs[id[i]].w);
+            ex[i] = exact_d2(ix.xyz64 + 3 * (size_t)cid[i], q64 + 3 * (size_t)qid);
+          } else {
+            cid[i] = 0xffffffffu;
+            ex[i] = INFINITY;
+          }
+        }
+        for (int pass = 0; pass < L; ++pass) {  // nearly sorted already: a few passes
+          bool sw = false;
+#pragma unroll
+          for (int i = 0; i + 1 < L; ++i) {
+            const bool gt = ex[i] > ex[i + 1] || (ex[i] == ex[i + 1] && cid[i] > cid[i + 1]);
+            if (gt) {
+              const double te = ex[i]; ex[i] = ex[i + 1]; ex[i + 1] = te;
+              const uint32_t tc = cid[i]; cid[i] = cid[i + 1]; cid[i + 1] = tc;
+              sw = true;
+            }
+          }
+          if (!sw) break;
+        }
+#pragma unroll
+        for (int i = 0; i < L; ++i) kth = fmax(kth, i < kk ? ex[i] : 0.0);  // ex ascending
+        undecided = !exhausted && !(kth < (double)W2);
+      }
+      if (undecided) {
+        if (found >= k && kk > 0 && kth < INFINITY) {
+          // the k-th value inside the box bounds the true k-th from above:
+          // the bounded search covers that sphere
+          const uint32_t e = atomicAdd(bcnt, 1u);
+          bslot[e] = qc + lane;
+          br2[e] = __double2float_ru(kth);
+        } else {
+          slow_list[atomicAdd(slow_cnt, 1u)] = qid;
+        }
+        continue;
+      }
+      int32_t* oi = out_idx + (size_t)qid * k;
+      double* od = out_d2 ? out_d2 + (size_t)qid * k : nullptr;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        if (i < k) {
+          const bool ok = i < kk;
+          oi[i] = ok ? (int32_t)cid[i] : -1;
+          if (od) od[i] = ok ? ex[i] : INFINITY;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ bounded search
+
+// Queries whose k-th neighbour may lie outside their group's box, with an
+// exact upper bound r2u on the true k-th squared distance (the k-th inside
+// the box): one warp per query visits every voxel meeting the sphere of
+// radius sqrt(r2u) (the range of Algorithm 1, widened by the proven pad),
+// keeps the candidates whose binary32 value is within the error band of
+// r2u (a superset of every point with d2 <= r2u, hence of the k nearest),
+// computes their binary64 values and sorts them by (d2, id).  More than
+// KB_CAP such candidates send the query to the ring-by-ring path.
+constexpr int KB_CAP = 1024;
+constexpr int KB_WARPS = 4;
+
+__global__ void __launch_bounds__(KB_WARPS * 32) knn_bounded_kernel(IndexView ix, QuerySet qs,
+                                                                     const Thresholds* __restrict__ thr_p, int k,
+                                                                     const uint32_t* __restrict__ bslot,
+                                                                     const float* __restrict__ br2,
+                                                                     const uint32_t* bcnt, int32_t* __restrict__ out_idx,
+                                                                     double* __restrict__ out_d2,
+                                                                     uint32_t* __restrict__ slow_list,
+                                                                     uint32_t* slow_cnt, const uint32_t* status) {
+  if (replan_pending(status)) return;
+  __shared__ double s_d2[KB_WARPS][KB_CAP];
+  __shared__ uint32_t s_id[KB_WARPS][KB_CAP];
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  double* wd2 = s_d2[warp];
+  uint32_t* wid = s_id[warp];
+  const Thresholds thr = *thr_p;
+  const KBound kb = make_kbound<1>(thr);
+  const float4* __restrict__ pts = ix.pts32;
+  const float4* __restrict__ qsrc = qs.all_points ? pts : qs.qrec;
+  const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
+  const int dim = ix.dim;
+  const uint32_t n = *bcnt;
+  for (uint32_t e = blockIdx.x * KB_WARPS + warp; e < n; e += gridDim.x * KB_WARPS) {
+    const float4 q = qsrc[bslot[e]];
+    const uint32_t qid = __float_as_uint(q.w);
+    const float r2u = br2[e];
+    const Tile& T = ix.tiles[(qs.all_points && ix.ntiles > 1) ? tile_of_id(ix.tiles, ix.ntiles, qid) : 0];
+    const float r = __fsqrt_ru(r2u);
+    const float qa[3] = {q.x, q.y, q.z};
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim) {
+        const float u = __fmul_rn(__fadd_rn(qa[a], T.D[a]), T.inv_sf[a]);
+        const float rr = __fmul_ru(__fmul_ru(r, T.inv_sf[a]), 1.0000005f);
+        float pad = __fadd_ru(__fadd_ru(rr, T.eta), __fmul_ru(__fadd_ru(fabsf(u), fabsf(qa[a]) * T.inv_sf[a]), 3.0e-7f));
+        pad = __fadd_ru(pad, __fmul_ru(thr.e_q, T.inv_sf[a]));
+        const float ul = fminf(fmaxf(__fsub_rd(u, pad), -1.0e9f), 1.0e9f);
+        const float uh = fminf(fmaxf(__fadd_ru(u, pad), -1.0e9f), 1.0e9f);
+        lo[a] = max((int)floorf(ul), 0);
+        hi[a] = min((int)floorf(uh), T.n[a] - 1);
+      } else {
+        lo[a] = 0;
+        hi[a] = T.n[a] - 1;
+      }
+    }
+    const float cut = __fadd_ru(r2u, 2.0f * kb.at(r2u));
+    uint32_t m = 0;
+    const int ni = hi[0] - lo[0] + 1, nj = hi[1] - lo[1] + 1;
+    const int ncol = (ni > 0 && nj > 0) ? (dim == 2 ? ni : ni * nj) : 0;
+    for (int cidx = 0; cidx < ncol; ++cidx) {
+      uint32_t k0, k1;
+      if (dim == 2) {
+        const uint32_t row = (uint32_t)(lo[0] + cidx) * (uint32_t)T.n[1];
+        k0 = T.key_base + row + (uint32_t)lo[1];
+        k1 = T.key_base + row + (uint32_t)hi[1];
+      } else {
+        const int i = lo[0] + cidx / nj, j = lo[1] + cidx % nj;
+        const uint32_t col = ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) * (uint32_t)T.n[2];
+        k0 = T.key_base + col + (uint32_t)lo[2];
+        k1 = T.key_base + col + (uint32_t)hi[2];
+      }
+      const uint2 sp = row_span(ix, T, k0, k1);
+      for (uint32_t t0 = sp.x; t0 < sp.y; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        bool pick = false;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < sp.y) {
+          p = __ldg(pts + t);
+          const float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
+          pick = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) <= cut;
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, pick);
+        const uint32_t pos = m + __popc(bm & lanemask_lt());
+        if (pick && pos < (uint32_t)KB_CAP) wid[pos] = __float_as_uint(p.w);
+        m += __popc(bm);
+      }
+    }
+    if (m > (uint32_t)KB_CAP || m < (uint32_t)k) {  // too many (or, impossibly, too few): the ring path
+      if (lane == 0) slow_list[atomicAdd(slow_cnt, 1u)] = qid;
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    int P = 32;
+    while (P < (int)m) P <<= 1;
+    for (int i = (int)lane; i < P; i += 32) {
+      if (i < (int)m) wd2[i] = exact_d2(ix.xyz64 + 3 * (size_t)wid[i], q64 + 3 * (size_t)qid);
+      else { wd2[i] = INFINITY; wid[i] = 0xffffffffu; }
+    }
+    __syncwarp();
+    warp_sort_list(wd2, wid, P);
+    for (int i = (int)lane; i < k; i += 32) {
+      out_idx[(size_t)qid * k + i] = (int32_t)wid[i];
+      if (out_d2) out_d2[(size_t)qid * k + i] = wd2[i];
+    }
+    __syncwarp();
   }
 }
 
@@ -488,6 +932,53 @@ __global__ void knn_thr_tiles_kernel(Thresholds* out, const Tile* __restrict__ t
 
 }  // namespace
 
+// Binary32 fast path for k <= 32: group boxes of radius 1 in two size
+// classes (staged boxes of <= 1024 and <= 2048 candidates; list length
+// k + 4 rounded up to 12, 20 or 36), then the bounded search of the queries
+// left undecided.  bslot / br2 have room for every query; ctrs[4..6] are
+// the box launches' group counters, ctrs[9] the bounded list's length,
+// ctrs[0] the ring-by-ring list's.
+cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Thresholds* thr, int k, int32_t* idx,
+                        double* d2, uint32_t* slow, uint32_t* bslot, float* br2, uint32_t* ctrs, uint32_t* status,
+                        cudaStream_t st) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+#define CG_K5(KC, L, NW, CLS)                                                                                \
+  do {                                                                                                       \
+    auto kfn = knn5_kernel<KC, L, NW>;                                                                       \
+    const size_t smem = K5Smem<KC>::per_warp_aligned * NW;                                                   \
+    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+    int per = 0;                                                                                             \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, NW * 32, smem);                                 \
+    ProfScope prof(CLS == 2 ? "knn5_2k" : (CLS ? "knn5_1k" : "knn5_512"), st);                               \
+    kfn<<<sms * (per > 0 ? per : 1), NW * 32, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, bslot, br2,    \
+                                                          ctrs + 9, ctrs + 4 + CLS, status, CLS);              \
+    note_launch();                                                                                           \
+  } while (0)
+  if (k <= 8) {
+    CG_K5(512, 12, 4, 0u);
+    CG_K5(1024, 12, 4, 1u);
+    CG_K5(2048, 12, 2, 2u);
+  } else if (k <= 16) {
+    CG_K5(512, 20, 4, 0u);
+    CG_K5(1024, 20, 4, 1u);
+    CG_K5(2048, 20, 2, 2u);
+  } else {
+    CG_K5(512, 36, 4, 0u);
+    CG_K5(1024, 36, 4, 1u);
+    CG_K5(2048, 36, 2, 2u);
+  }
+#undef CG_K5
+  {
+    ProfScope prof("knn_bounded", st);
+    knn_bounded_kernel<<<sms * 4, KB_WARPS * 32, 0, st>>>(iv, qs, thr, k, bslot, br2, ctrs + 9, idx, d2, slow, ctrs,
+                                                          status);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx, double* d2,
                    cudaStream_t st) {
   if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
@@ -501,9 +992,12 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   if (nq == 0) return CG_OK;
   DevBufs tmp;
   uint32_t* slow = (uint32_t*)tmp.get(4 * (size_t)nq, st);
+  // queries for the bounded search (room for every query)
+  uint32_t* bslot = (uint32_t*)tmp.get(4 * (size_t)nq, st);
+  float* br2 = (float*)tmp.get(4 * (size_t)nq, st);
   uint32_t* ctrs = (uint32_t*)tmp.get(256, st);
   Thresholds* thr = (Thresholds*)tmp.get(sizeof(Thresholds), st);
-  if (!slow || !ctrs || !thr) { tmp.release(st); return fail(CG_ERR_OOM, "device allocation failed (k-NN)"); }
+  if (!slow || !ctrs || !thr || !bslot || !br2) { tmp.release(st); return fail(CG_ERR_OOM, "device allocation failed (k-NN)"); }
   cudaError_t e = cudaMemsetAsync(ctrs, 0, 256, st);
   double emax = 0;
   for (const Tile& T : ix->tiles_host) emax = std::max(emax, (double)T.enc_err);
@@ -539,7 +1033,14 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const IndexView iv = ix->view();
-  if (ix->precision == CG_FP32_OFFSET) {
+  if (ix->precision == CG_FP32_OFFSET && k <= 32) {
+    e = launch_knn5(iv, qs, thr, k, idx, d2, slow, bslot, br2, ctrs, C.status, st);
+    {
+      ProfScope prof("knn_slow", st);
+      knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2);
+    }
+    note_launch();
+  } else if (ix->precision == CG_FP32_OFFSET) {
     const size_t smem = knn_smem<1>();
     cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
@@ -582,9 +1083,12 @@ cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, i
 
 cg_status knn_work_alloc(cg_index* ix, KnnWork& w, cudaStream_t st) {
   w.slow = (uint32_t*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->n, 1), st);
+  w.bslot = (uint32_t*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->n, 1), st);
+  w.br2 = (float*)w.bufs.get(4 * (size_t)std::max<int64_t>(ix->n, 1), st);
   w.ctrs = (uint32_t*)w.bufs.get(256, st);
   w.thr = (Thresholds*)w.bufs.get(sizeof(Thresholds), st);
-  if (!w.slow || !w.ctrs || !w.thr) return fail(CG_ERR_OOM, "device allocation failed (pipeline k-NN work)");
+  if (!w.slow || !w.ctrs || !w.thr || !w.bslot || !w.br2)
+    return fail(CG_ERR_OOM, "device allocation failed (pipeline k-NN work)");
   return CG_OK;
 }
 
@@ -610,7 +1114,10 @@ cg_status knn_replay(cg_index* ix, KnnWork& w, const uint32_t* nkeys_dev, uint32
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const IndexView iv = ix->view();
-  if (ix->precision == CG_FP32_OFFSET) {
+  if (ix->precision == CG_FP32_OFFSET && k <= 32) {
+    e = launch_knn5(iv, qs, w.thr, k, idx, d2, w.slow, w.bslot, w.br2, w.ctrs, ix->status, st);
+    knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, w.slow, w.ctrs, idx, d2); note_launch();
+  } else if (ix->precision == CG_FP32_OFFSET) {
     const size_t smem = knn_smem<1>();
     cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
