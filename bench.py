@@ -139,6 +139,26 @@ def _setup_dist(args):
     return rank, world, local, dist
 
 
+def _max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (every rank gets it); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x: float, dist, device) -> float:
+    """Total over ranks (units of work processed by the whole job)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _cpu_baseline(xyz, sample_queries: int, seed: int = 5):
     """The oracle as it stands, on the host cores: full single-threaded build
     plus a seeded sample of queries on all cores, extrapolated to N queries."""
@@ -304,11 +324,7 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = _max_over_ranks(t0.elapsed_time(t1) / args.steps, dist, dev)
     build_ms = statistics.mean(r[0].elapsed_time(r[1]) for r in records)
     count_ms = statistics.mean(r[1].elapsed_time(r[2]) for r in records)
     fill_ms = statistics.mean(r[2].elapsed_time(r[3]) for r in records)
@@ -337,7 +353,9 @@ def run_ours(args):
             e2e_times.append(a.elapsed_time(b))
     e2e_ms = statistics.mean(e2e_times)
 
-    value = world * n / (ms * 1e-3)
+    n_all = _sum_over_ranks(n, dist, dev)          # queries of the whole job
+    total_all = _sum_over_ranks(total, dist, dev)  # neighbours of the whole job
+    value = n_all / (ms * 1e-3)
     peak, peak_kind = _peaks()
     per_step = {k: v[1] / args.steps for k, v in phases.items()}
     # the count (fill) kernels of one pass run concurrently on forked
@@ -403,16 +421,18 @@ def run_ours(args):
         "config": {"workload": "ALS tile 12M pts, 500x500 m, 2D dense grid 1 m, sphere r=1 m, all points as queries",
                    "n_points": n, "radius_m": RADIUS, "cell_m": CELL, "precision": args.precision,
                    "l2": "inputs larger than L2 (288 MB points, 129 MB L2)", "parallelism": f"replicas x{world}"},
-        "neighbors_per_s": world * total / (ms * 1e-3), "neighbors_per_step": total,
+        "neighbors_per_s": total_all / (ms * 1e-3), "neighbors_per_step": total_all,
         "stages_ms": {"build": build_ms, "count": count_ms, "fill": fill_ms},
         "kernels_ms_per_step": per_step,
-        "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": n_all / (_max_over_ranks(e2e_ms, dist, dev) * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": (n + 1) * 8 + total * 4},
         "roofline": roof, "clocks": clk, "gpu_launches": launches,
-        "knn16": {"queries_per_s": world * n / (statistics.mean(kt) * 1e-3), "ms": statistics.mean(kt)},
+        "knn16": {"queries_per_s": n_all / (_max_over_ranks(statistics.mean(kt), dist, dev) * 1e-3),
+                  "ms": statistics.mean(kt)},
     }
     if fp64_ms is not None:
-        line["fp64_path"] = {"queries_per_s": world * n / (fp64_ms * 1e-3), "ms_per_step": fp64_ms}
+        line["fp64_path"] = {"queries_per_s": n_all / (_max_over_ranks(fp64_ms, dist, dev) * 1e-3),
+                             "ms_per_step": fp64_ms}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(xyz, args.cpu_sample)
     if rank == 0:
@@ -463,11 +483,7 @@ def run_batched(args):
         launches = (cg.cg_launch_count() - l0) / args.steps
         total = pipe.run()  # synchronising check: no re-plan, no device error
         assert pipe.info()["replans"] == 0
-        ms = a.elapsed_time(b) / args.steps
-        if dist is not None:
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = _max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
         info = pipe.info()
         # end to end: pinned host points in, CSR and k-NN out, every step
         host_in = torch.from_numpy(xyz).pin_memory()
