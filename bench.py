@@ -115,7 +115,7 @@ def _src_hash(names) -> str:
 def _traffic(kernel: str, src_files) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current source of the kernel."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic_radius_als12m.txt")
     try:
         with open(path) as f:
             t = json.load(f)
@@ -251,6 +251,8 @@ def _alg_tests(xyz, r: float, cell: float) -> int:
 # binary32 lane operations of one sphere test: 3 subtractions, 1 multiply,
 # 2 fused multiply-adds, 1 comparison
 OPS_PER_TEST = 7
+# sources of the kernels whose DRAM traffic profiles/traffic.json records
+TRAFFIC_SRC = ["cg_radius2.cu", "cg_query.cu", "cg_query.cuh", "cg_internal.cuh"]
 COUNT_PHASES = ("radius_count5_1k", "radius_count5_2k", "radius_count2", "radius_v1_count")
 FILL_PHASES = ("radius_fill5_1k", "radius_fill5_2k", "radius_fill2", "radius_v1_fill", "radius_row_sort")
 
@@ -373,7 +375,7 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": "concurrent " + "+".join(k for k in COUNT_PHASES if k in per_step),
                 "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s", "frac": achieved / alu_peak,
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
-                "traffic": _traffic("radius_count5_1k", ["cg_radius2.cu", "cg_query.cuh", "cg_internal.cuh"]),
+                "traffic": _traffic("radius_count_kernels", TRAFFIC_SRC),
                 "algorithmic_tests": tests, "ops_per_test": OPS_PER_TEST, "ms_per_launch": count_k}
     else:
         alg = 16 * n + 4 * (ncell + 1) + 8 * (n + 1) + 4 * total
@@ -381,7 +383,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": "concurrent " + "+".join(k for k in FILL_PHASES if k in per_step),
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": _traffic("radius_fill5_1k", ["cg_radius2.cu", "cg_query.cuh", "cg_internal.cuh"]),
+                "traffic": _traffic("radius_fill_kernels", TRAFFIC_SRC),
                 "algorithmic_bytes": alg, "ms_per_launch": fill_k}
 
     # secondary measurements on the same tile: k-NN (k = 16) and the binary64 path
