@@ -727,19 +727,24 @@ __global__ void __launch_bounds__(KB_WARPS * 32) knn_bounded_kernel(IndexView ix
         k1 = T.key_base + col + (uint32_t)hi[2];
       }
       const uint2 sp = row_span(ix, T, k0, k1);
-      for (uint32_t t0 = sp.x; t0 < sp.y; t0 += 32) {
-        const uint32_t t = t0 + lane;
-        bool pick = false;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < sp.y) {
-          p = __ldg(pts + t);
-          const float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
-          pick = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) <= cut;
+      for (uint32_t t0 = sp.x; t0 < sp.y; t0 += 128) {  // four loads in flight per lane
+        float4 p[4];
+        bool pick[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t t = t0 + 32u * u + lane;
+          pick[u] = t < sp.y;
+          p[u] = pick[u] ? __ldg(pts + t) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const unsigned bm = __ballot_sync(0xffffffffu, pick);
-        const uint32_t pos = m + __popc(bm & lanemask_lt());
-        if (pick && pos < (uint32_t)KB_CAP) wid[pos] = __float_as_uint(p.w);
-        m += __popc(bm);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float dx = __fsub_rn(p[u].x, q.x), dy = __fsub_rn(p[u].y, q.y), dz = __fsub_rn(p[u].z, q.z);
+          pick[u] = pick[u] && __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) <= cut;
+          const unsigned bm = __ballot_sync(0xffffffffu, pick[u]);
+          const uint32_t pos = m + __popc(bm & lanemask_lt());
+          if (pick[u] && pos < (uint32_t)KB_CAP) wid[pos] = __float_as_uint(p[u].w);
+          m += __popc(bm);
+        }
       }
     }
     if (m > (uint32_t)KB_CAP || m < (uint32_t)k) {  // too many (or, impossibly, too few): the ring path
@@ -944,6 +949,9 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // the classes' groups are disjoint: their launches run concurrently
+  ProfScope prof_all("knn_fast_kernels", st);  // box classes + bounded search
+  Fork f(st, 3);
 #define CG_K5(KC, L, NW, CLS)                                                                                \
   do {                                                                                                       \
     auto kfn = knn5_kernel<KC, L, NW>;                                                                       \
@@ -951,8 +959,9 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
     int per = 0;                                                                                             \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, NW * 32, smem);                                 \
-    ProfScope prof(CLS == 2 ? "knn5_2k" : (CLS ? "knn5_1k" : "knn5_512"), st);                               \
-    kfn<<<sms * (per > 0 ? per : 1), NW * 32, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, bslot, br2,    \
+    cudaStream_t cs = f[CLS];                                                                                \
+    ProfScope prof(CLS == 2 ? "knn5_2k" : (CLS ? "knn5_1k" : "knn5_512"), cs);                               \
+    kfn<<<sms * (per > 0 ? per : 1), NW * 32, smem, cs>>>(iv, qs, thr, k, idx, d2, slow, ctrs, bslot, br2,    \
                                                           ctrs + 9, ctrs + 4 + CLS, status, CLS);              \
     note_launch();                                                                                           \
   } while (0)
@@ -970,6 +979,7 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
     CG_K5(2048, 36, 2, 2u);
   }
 #undef CG_K5
+  f.join();
   {
     ProfScope prof("knn_bounded", st);
     knn_bounded_kernel<<<sms * 4, KB_WARPS * 32, 0, st>>>(iv, qs, thr, k, bslot, br2, ctrs + 9, idx, d2, slow, ctrs,
