@@ -88,8 +88,14 @@ struct AuxStreams {
     if (ok && d == dev) return true;
     release();
     bool good = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    // the last branch carries the longest single blocks of a pass (the
+    // general kernel's largest groups): it gets the highest priority so that
+    // they start first instead of ending the pass
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
     for (int i = 0; good && i < Fork::kMax - 1; ++i)
-      good = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess &&
+      good = cudaStreamCreateWithPriority(&s[i], cudaStreamNonBlocking, i == Fork::kMax - 2 ? greatest : least) ==
+                 cudaSuccess &&
              cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
     cudaGetLastError();
     ok = good;

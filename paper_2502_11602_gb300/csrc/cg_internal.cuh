@@ -62,7 +62,8 @@ void note_launch(int n = 1);
 // set per host thread and device), so that they overlap on the GPU: every
 // branch starts after the work already on the origin stream, and the origin
 // continues only after every branch.  Works inside a stream capture (the
-// branches become parallel graph nodes).
+// branches become parallel graph nodes).  Branch kMax - 1 runs at the
+// device's highest stream priority.
 struct Fork {
   static constexpr int kMax = 4;
   Fork(cudaStream_t origin, int branches);

@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
 template <int KC>
 struct F5 {
   static constexpr int WMAX = KC / 32;
-  static constexpr int ROW = KC > 1024 ? KC : 1024;  // staging entries
+  static constexpr int ROW = KC > 1024 ? KC : 0;  // staging entries (two-word rows only)
   static constexpr size_t per_warp = 4 * (size_t)KC + 4 * (size_t)WMAX * 33 + 4 * (size_t)ROW + 8 * 32;
 };
 
@@ -848,8 +848,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
       }
       __syncwarp();
       if (L::WMAX <= 32 || Wp <= 32) {
+        // each word's hits go straight to their place in the row
         const uint32_t rows = 32u / seg, j = lane / seg, wl = lane % seg;
-        int32_t* srow = row + j * seg * 32u;
         for (uint32_t t0 = 0; t0 < nc; t0 += rows) {
           const uint32_t t = t0 + j;
           const bool live = t < nc;
@@ -860,19 +860,12 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o, seg);
             if (wl >= o) incl += y;
           }
-          const uint32_t tot = __shfl_sync(0xffffffffu, incl, seg - 1, seg);
-          uint32_t p = incl - c;
+          int32_t* dst = out + (live ? soff[t] : 0) + (incl - c);
           while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
-            srow[p++] = (int32_t)sids[wl * 32 + bit];
+            *dst++ = (int32_t)sids[wl * 32 + bit];
           }
-          __syncwarp();
-          if (live) {
-            int32_t* dst = out + soff[t];
-            for (uint32_t i = wl; i < tot; i += seg) dst[i] = srow[i];
-          }
-          __syncwarp();
         }
       } else {
         for (uint32_t t = 0; t < nc; ++t) {
