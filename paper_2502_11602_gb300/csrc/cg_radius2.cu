@@ -540,8 +540,9 @@ struct C5 {
   static constexpr size_t PH1 = 4 * (size_t)KC + 4 * (size_t)NBK + 2 * (size_t)KC;  // ids, buckets, order
   static constexpr size_t R1 = ((PH2 > PH1 ? PH2 : PH1) + 15) / 16 * 16;
   static constexpr size_t SLOT = 2 * (size_t)KC;                                    // id-order slot of each candidate
-  static constexpr size_t RUNS = 4 * (2 * 36 + 32);
-  static constexpr size_t per_warp = (R1 + SLOT + RUNS + 15) / 16 * 16;
+  static constexpr size_t RUNS = 4 * (2 * 36 + 4 + 2 * 4);
+  // a slot of gw warps: the group's tables plus 32 query counters per warp
+  __host__ __device__ static constexpr size_t per_slot(int gw) { return (R1 + SLOT + RUNS + 4 * 32 * (size_t)gw + 15) / 16 * 16; }
 };
 
 template <int KERN>
@@ -560,7 +561,16 @@ __device__ __forceinline__ void pair_test(const ulonglong2& xy, unsigned long lo
   }
 }
 
-template <int KERN, int KC, int NWARP>
+// GW warps share a group (a slot of the CTA): they stage and sort its
+// candidates together (per-slot named barriers), then each takes its own
+// chunks of 32 queries.  GW = 1 for the smallest size class.
+template <int GW>
+__device__ __forceinline__ void slot_sync(int slot) {
+  if (GW == 1) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(GW * 32) : "memory");
+}
+
+template <int KERN, int KC, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix, QuerySet qs,
                                                                    const Thresholds* __restrict__ thr_p,
                                                                    const BlockPlan* __restrict__ plans,
@@ -572,8 +582,12 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
                                                                    const uint32_t* status, uint32_t cls) {
   if (replan_pending(status)) return;
   using L = C5<KC>;
+  constexpr int ST = GW * 32;  // threads per slot
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * L::per_warp;
+  const unsigned lane = threadIdx.x & 31u;
+  const int warp = (int)(threadIdx.x >> 5), slot = warp / GW, wis = warp % GW;
+  const uint32_t tis = (uint32_t)wis * 32u + lane;  // thread in slot
+  unsigned char* base = smem + (size_t)slot * L::per_slot(GW);
   uint32_t* ids_r = reinterpret_cast<uint32_t*>(base);           // phase 1: ids in run order
   uint32_t* bk = ids_r + KC;                                      // phase 1: bucket counters
   uint16_t* order = reinterpret_cast<uint16_t*>(bk + L::NBK);     // phase 1: id order -> run position
@@ -583,8 +597,9 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   uint16_t* slot_of = reinterpret_cast<uint16_t*>(base + L::R1);  // run position -> id order
   uint32_t* rstart = reinterpret_cast<uint32_t*>(base + L::R1 + L::SLOT);
   uint32_t* roff = rstart + 36;
-  uint32_t* qcnt = roff + 36;  // [32] hits of the current 32 queries
-  const unsigned lane = threadIdx.x & 31u;
+  uint32_t* sbox = roff + 36;                  // [4]: group, crowded flag, id range
+  uint32_t* wred = sbox + 4;                   // [2 GW]: per-warp id minima / maxima
+  uint32_t* qcnt = wred + 2 * 4 + 32 * wis;    // [32] per warp: hits of its current 32 queries
   const Thresholds thr = *thr_p;
   const float4* __restrict__ pts = ix.pts32;
   const uint32_t* __restrict__ sid = ix.sid;
@@ -594,23 +609,24 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   const float shi = KERN == CG_SPHERE ? thr.s_hi : thr.c_hi;
   const float far = __int_as_float(0x7f000000);  // padding candidate: its square overflows to +inf
   for (;;) {
-    uint32_t b = 0;
-    if (lane == 0) b = atomicAdd(work, 1u);
-    b = __shfl_sync(0xffffffffu, b, 0);
+    if (tis == 0) sbox[0] = atomicAdd(work, 1u);
+    slot_sync<GW>(slot);
+    const uint32_t b = sbox[0];
+    slot_sync<GW>(slot);
     if (b >= qs_nblocks(qs)) break;
     const uint32_t* hp = reinterpret_cast<const uint32_t*>(plans + b);
     const uint32_t q0 = __ldg(hp), nq = __ldg(hp + 1), K = __ldg(hp + 2);
     const uint32_t nsp = __ldg(hp + 3) & 0xffffu, heavy = __ldg(hp + 4), gcls = __ldg(hp + 5);
     if (heavy || gcls != cls || nq == 0) continue;
     if (K == 0) {
-      for (uint32_t t = lane; t < nq; t += 32) counts[__float_as_uint(qsrc[q0 + t].w)] = 0;
+      for (uint32_t t = tis; t < nq; t += ST) counts[__float_as_uint(qsrc[q0 + t].w)] = 0;
       continue;
     }
     uint32_t* mb = masks + moff[b];
     const uint32_t io = idoff[b];
     const uint32_t Wp = (K + 31u) / 32u;
     // runs and their offsets in the run-order concatenation
-    {
+    if (wis == 0) {
       const uint32_t rl = lane < nsp ? __ldg(plans[b].len + lane) : 0u;
       uint32_t incl = rl;
       for (int o = 1; o < 32; o <<= 1) {
@@ -623,12 +639,12 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       }
       if (lane == 0) roff[nsp] = K;
     }
-    __syncwarp();
+    slot_sync<GW>(slot);
     // 1. ids, run by run
     uint32_t mn = 0xffffffffu, mx = 0u;
     for (uint32_t r = 0; r < nsp; ++r) {
       const uint32_t o = roff[r], len = roff[r + 1] - o, s0 = rstart[r];
-      for (uint32_t t = lane; t < len; t += 32) {
+      for (uint32_t t = tis; t < len; t += ST) {
         const uint32_t id = __ldg(sid + s0 + t);
         ids_r[o + t] = id;
         mn = min(mn, id);
@@ -637,16 +653,22 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
     }
     mn = __reduce_min_sync(0xffffffffu, mn);
     mx = __reduce_max_sync(0xffffffffu, mx);
+    if (GW > 1) {
+      if (lane == 0) { wred[wis] = mn; wred[GW + wis] = mx; }
+      slot_sync<GW>(slot);
+#pragma unroll
+      for (int w = 0; w < GW; ++w) { mn = min(mn, wred[w]); mx = max(mx, wred[GW + w]); }
+    }
     int shift = 0;
     while (shift < 31 && ((mx - mn) >> shift) >= (uint32_t)L::NBK) ++shift;
-    for (uint32_t u = lane; u < (uint32_t)L::NBK; u += 32) bk[u] = 0u;
-    __syncwarp();
-    for (uint32_t p = lane; p < K; p += 32) atomicAdd(&bk[(ids_r[p] - mn) >> shift], 1u);
-    __syncwarp();
-    // 2. exclusive scan of the buckets (a contiguous chunk per lane)
+    for (uint32_t u = tis; u < (uint32_t)L::NBK; u += ST) bk[u] = 0u;
+    slot_sync<GW>(slot);
+    for (uint32_t p = tis; p < K; p += ST) atomicAdd(&bk[(ids_r[p] - mn) >> shift], 1u);
+    slot_sync<GW>(slot);
+    // 2. exclusive scan of the buckets (warp 0 of the slot, a contiguous chunk per lane)
     constexpr int PER = L::NBK / 32;
-    bool crowded = false;
-    {
+    if (wis == 0) {
+      bool crowded = false;
       uint32_t c[PER], sum = 0;
 #pragma unroll
       for (int u = 0; u < PER; ++u) {
@@ -665,13 +687,14 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
         bk[PER * lane + u] = pre;
         pre += c[u];
       }
+      crowded = __any_sync(0xffffffffu, crowded);
+      if (lane == 0) sbox[1] = crowded ? 1u : 0u;
     }
-    crowded = __any_sync(0xffffffffu, crowded);
-    __syncwarp();
-    if (!crowded) {
-      for (uint32_t p = lane; p < K; p += 32) order[atomicAdd(&bk[(ids_r[p] - mn) >> shift], 1u)] = (uint16_t)p;
-      __syncwarp();
-      for (uint32_t u = lane; u < (uint32_t)L::NBK; u += 32) {  // bucket u now spans [bk[u-1], bk[u])
+    slot_sync<GW>(slot);
+    if (!sbox[1]) {
+      for (uint32_t p = tis; p < K; p += ST) order[atomicAdd(&bk[(ids_r[p] - mn) >> shift], 1u)] = (uint16_t)p;
+      slot_sync<GW>(slot);
+      for (uint32_t u = tis; u < (uint32_t)L::NBK; u += ST) {  // bucket u now spans [bk[u-1], bk[u])
         const uint32_t e1 = bk[u], e0 = u ? bk[u - 1] : 0u;
         for (uint32_t x = e0 + 1; x < e1; ++x) {
           const uint16_t g = order[x];
@@ -688,7 +711,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       // ids packed into a narrow range: merge the sorted runs by rank
       for (uint32_t r = 0; r < nsp; ++r) {
         const uint32_t o = roff[r], len = roff[r + 1] - o;
-        for (uint32_t t = lane; t < len; t += 32) {
+        for (uint32_t t = tis; t < len; t += ST) {
           const uint32_t id = ids_r[o + t];
           uint32_t rank = t;
           for (uint32_t r2 = 0; r2 < nsp; ++r2) {
@@ -706,17 +729,17 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
         }
       }
     }
-    __syncwarp();
-    for (uint32_t j = lane; j < K; j += 32) {
+    slot_sync<GW>(slot);
+    for (uint32_t j = tis; j < K; j += ST) {
       const uint32_t p = order[j];
       slot_of[p] = (uint16_t)j;
       ids[io + j] = ids_r[p];
     }
-    __syncwarp();
+    slot_sync<GW>(slot);
     // 3. records into their id-order slots (overwrites the phase-1 tables)
     for (uint32_t r = 0; r < nsp; ++r) {
       const uint32_t o = roff[r], len = roff[r + 1] - o, s0 = rstart[r];
-      for (uint32_t t = lane; t < len; t += 32) {
+      for (uint32_t t = tis; t < len; t += ST) {
         const float4 rec = __ldg(pts + s0 + t);
         const int ps = pair_slot(slot_of[o + t]), h = slot_of[o + t] & 1;
         float* xy = reinterpret_cast<float*>(PL.xy + ps);
@@ -726,7 +749,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
         z[h] = rec.z;
       }
     }
-    for (uint32_t j = K + lane; j < Wp * 32u; j += 32) {
+    for (uint32_t j = K + tis; j < Wp * 32u; j += ST) {
       const int ps = pair_slot((int)j), h = (int)(j & 1u);
       float* xy = reinterpret_cast<float*>(PL.xy + ps);
       float* z = reinterpret_cast<float*>(PL.z + ps);
@@ -734,9 +757,9 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       xy[2 + h] = far;
       z[h] = far;
     }
-    __syncwarp();
-    // 4. tests: lanes = (query, slice of words); Sl lanes share a query
-    for (uint32_t qg0 = 0; qg0 < nq; qg0 += 32) {
+    slot_sync<GW>(slot);
+    // 4. tests: each warp its own chunks of 32 queries; lanes = (query, slice of words)
+    for (uint32_t qg0 = 32u * wis; qg0 < nq; qg0 += 32u * GW) {
       const uint32_t nqg = min(32u, nq - qg0);
       const uint32_t Sl = min(Wp, 32u / nqg);
       const uint32_t qi = lane / Sl, s = lane - qi * Sl;
@@ -786,25 +809,28 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       if (active && s == 0) counts[qid] = qcnt[qi];
       __syncwarp();
     }
+    slot_sync<GW>(slot);  // the next group overwrites the slot's tables
   }
 }
 
-// Fill of the binary32 groups: the group's sorted ids to shared memory, then
-// per chunk of 32 queries their masks (word-major, one coalesced row per
-// word).  Rows are expanded in lane segments of seg = 2^ceil(log2 Wp) lanes,
+// Fill of the binary32 groups: the group's sorted ids to shared memory
+// (once per slot of GW warps), then each warp takes its own chunks of 32
+// queries: their masks (word-major, one coalesced row per word) to shared
+// memory; rows are expanded in lane segments of seg = 2^ceil(log2 Wp) lanes,
 // 32 / seg rows at a time (one word per lane): a segmented scan of the
-// words' popcounts places each word's hits, the bits are expanded (ascending
-// ids) into the segment's staging row, and the segment writes its row out
-// with coalesced stores.  Groups of more than 32 words use the whole warp
-// per row, two words per lane.
+// words' popcounts places each word's hits, whose ids (ascending) go
+// straight to their place in the row.  Groups of more than 32 words use the
+// whole warp per row, words 32..63 placed after all of words 0..31.
 template <int KC>
 struct F5 {
   static constexpr int WMAX = KC / 32;
-  static constexpr int ROW = KC > 1024 ? KC : 0;  // staging entries (two-word rows only)
-  static constexpr size_t per_warp = 4 * (size_t)KC + 4 * (size_t)WMAX * 33 + 4 * (size_t)ROW + 8 * 32;
+  __host__ __device__ static constexpr size_t per_warp() { return 4 * (size_t)WMAX * 33 + 8 * 32; }
+  __host__ __device__ static constexpr size_t per_slot(int gw) {
+    return (4 * (size_t)KC + per_warp() * (size_t)gw + 15) / 16 * 16;
+  }
 };
 
-template <int KC, int NWARP>
+template <int KC, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, QuerySet qs,
                                                                   const BlockPlan* __restrict__ plans,
                                                                   const uint32_t* __restrict__ moff,
@@ -816,18 +842,23 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
                                                                   const uint32_t* status, uint32_t cls) {
   if (replan_pending(status)) return;
   using L = F5<KC>;
+  constexpr int ST = GW * 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * L::per_warp;
-  uint32_t* sids = reinterpret_cast<uint32_t*>(base);             // [KC]
-  uint32_t* ms = sids + KC;                                        // [WMAX][33]
-  int32_t* row = reinterpret_cast<int32_t*>(ms + L::WMAX * 33);   // [ROW]
-  long long* soff = reinterpret_cast<long long*>(row + L::ROW);  // [32]
+  __shared__ uint32_t s_grp[NWARP / GW];
   const unsigned lane = threadIdx.x & 31u;
+  const int warp = (int)(threadIdx.x >> 5), slot = warp / GW, wis = warp % GW;
+  const uint32_t tis = (uint32_t)wis * 32u + lane;
+  unsigned char* base = smem + (size_t)slot * L::per_slot(GW);
+  uint32_t* sids = reinterpret_cast<uint32_t*>(base);                                  // [KC]
+  unsigned char* wbase = base + 4 * (size_t)KC + (size_t)wis * L::per_warp();
+  uint32_t* ms = reinterpret_cast<uint32_t*>(wbase);                                   // [WMAX][33]
+  long long* soff = reinterpret_cast<long long*>(ms + L::WMAX * 33);                  // [32]
   const float4* __restrict__ qsrc = qs.all_points ? ix.pts32 : qs.qrec;
   for (;;) {
-    uint32_t b = 0;
-    if (lane == 0) b = atomicAdd(work, 1u);
-    b = __shfl_sync(0xffffffffu, b, 0);
+    if (tis == 0) s_grp[slot] = atomicAdd(work, 1u);
+    slot_sync<GW>(slot);
+    const uint32_t b = s_grp[slot];
+    slot_sync<GW>(slot);
     if (b >= qs_nblocks(qs)) break;
     const uint32_t* hp = reinterpret_cast<const uint32_t*>(plans + b);
     const uint32_t q0 = __ldg(hp), nq = __ldg(hp + 1), K = __ldg(hp + 2);
@@ -836,10 +867,11 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
     const uint32_t Wp = (K + 31u) / 32u;
     const uint32_t io = idoff[b];
     const uint32_t* __restrict__ mb = masks + moff[b];
-    for (uint32_t j = lane; j < K; j += 32) sids[j] = __ldg(ids + io + j);
+    for (uint32_t j = tis; j < K; j += ST) sids[j] = __ldg(ids + io + j);
+    slot_sync<GW>(slot);
     uint32_t seg = 1;
     while (seg < Wp && seg < 32) seg <<= 1;
-    for (uint32_t c0 = 0; c0 < nq; c0 += 32) {
+    for (uint32_t c0 = 32u * wis; c0 < nq; c0 += 32u * GW) {
       const uint32_t nc = min(32u, nq - c0);
       __syncwarp();
       if (lane < nc) {
@@ -870,6 +902,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
       } else {
         for (uint32_t t = 0; t < nc; ++t) {
           // words 0..31 (lane = word), then words 32..63 after all of them
+          int32_t* row = out + soff[t];
           uint32_t tot = 0;
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
@@ -881,21 +914,18 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
               const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
               if (lane >= (unsigned)o) incl += y;
             }
-            uint32_t p = tot + incl - c;
+            int32_t* dst = row + tot + (incl - c);
             tot += __shfl_sync(0xffffffffu, incl, 31);
             while (m) {
               const int bit = __ffs(m) - 1;
               m &= m - 1;
-              row[p++] = (int32_t)sids[w * 32 + bit];
+              *dst++ = (int32_t)sids[w * 32 + bit];
             }
           }
-          __syncwarp();
-          int32_t* dst = out + soff[t];
-          for (uint32_t i = lane; i < tot; i += 32) dst[i] = row[i];
-          __syncwarp();
         }
       }
     }
+    slot_sync<GW>(slot);  // the next group overwrites the slot's ids
   }
 }
 
@@ -1069,12 +1099,13 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
                                   const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
                                   uint32_t* status, const cudaStream_t* sts) {
-  // size classes: K <= 512 and <= 1024 (4 warps per CTA), <= 2048 (2 warps);
-  // work[0..2] are their group counters, sts[0..2] their streams
-#define CG_C5(KN, KC, NW, CLS, WORK)                                                             \
+  // size classes: K <= 512 (a warp per group), <= 1024 (two warps per
+  // group), <= 2048 (four); 4 warps per CTA; work[0..2] are their group
+  // counters, sts[0..2] their streams
+#define CG_C5(KN, KC, NW, GW, CLS, WORK)                                                         \
   do {                                                                                            \
-    auto kfn = radius_count5_kernel<KN, KC, NW>;                                                 \
-    const size_t smem = C5<KC>::per_warp * NW;                                                   \
+    auto kfn = radius_count5_kernel<KN, KC, NW, GW>;                                             \
+    const size_t smem = C5<KC>::per_slot(GW) * (NW / GW);                                        \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
     cudaStream_t st = sts[CLS];                                                                  \
@@ -1084,13 +1115,13 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
     note_launch();                                                                                \
   } while (0)
   if (kern == CG_SPHERE) {
-    CG_C5(CG_SPHERE, 512, 4, 0u, work);
-    CG_C5(CG_SPHERE, 1024, 4, 1u, work + 1);
-    CG_C5(CG_SPHERE, 2048, 2, 2u, work + 2);
+    CG_C5(CG_SPHERE, 512, 4, 1, 0u, work);
+    CG_C5(CG_SPHERE, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_SPHERE, 2048, 4, 4, 2u, work + 2);
   } else {
-    CG_C5(CG_CUBE, 512, 4, 0u, work);
-    CG_C5(CG_CUBE, 1024, 4, 1u, work + 1);
-    CG_C5(CG_CUBE, 2048, 2, 2u, work + 2);
+    CG_C5(CG_CUBE, 512, 4, 1, 0u, work);
+    CG_C5(CG_CUBE, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_CUBE, 2048, 4, 4, 2u, work + 2);
   }
 #undef CG_C5
   return cudaGetLastError();
@@ -1100,10 +1131,10 @@ cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const 
                                  const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                  const uint32_t* status, const cudaStream_t* sts) {
-#define CG_F5(KC, NW, CLS, WORK)                                                                  \
+#define CG_F5(KC, NW, GW, CLS, WORK)                                                              \
   do {                                                                                            \
-    auto kfn = radius_fill5_kernel<KC, NW>;                                                      \
-    const size_t smem = F5<KC>::per_warp * NW;                                                   \
+    auto kfn = radius_fill5_kernel<KC, NW, GW>;                                                  \
+    const size_t smem = F5<KC>::per_slot(GW) * (NW / GW);                                        \
     cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
     cudaStream_t st = sts[CLS];                                                                  \
@@ -1111,9 +1142,9 @@ cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const 
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, WORK, status, CLS); \
     note_launch();                                                                                \
   } while (0)
-  CG_F5(512, 4, 0u, work);
-  CG_F5(1024, 4, 1u, work + 1);
-  CG_F5(2048, 2, 2u, work + 2);
+  CG_F5(512, 4, 1, 0u, work);
+  CG_F5(1024, 4, 2, 1u, work + 1);
+  CG_F5(2048, 4, 4, 2u, work + 2);
 #undef CG_F5
   return cudaGetLastError();
 }
