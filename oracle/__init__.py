@@ -31,7 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 DENSE, SPARSE, MIXED = 0, 1, 2
-SPHERE, CUBE = 0, 1
+SPHERE, CUBE, CYLINDER = 0, 1, 2
 
 _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 

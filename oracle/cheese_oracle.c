@@ -25,7 +25,9 @@
  *                      here a sorted key array searched by bisection).
  *   mixed flavour   -- Section 3.3.3 (z slices, each dense iff at least 80 %
  *                      of its voxels are non-empty; 2D = one slice).
- *   kernel search   -- Algorithm 1 (bounding box -> voxel range -> scan).
+ *   kernel search   -- Algorithm 1 (bounding box -> voxel range -> scan);
+ *                      kernels: sphere, cube, and the vertical cylinder
+ *                      (xy only, z unbounded) of Section 2.
  *   k-NN            -- Algorithm 2 (growing radius + taboo box, Section 3.5).
  *   brute force     -- the definition of both result sets (Section 2).
  *
@@ -46,6 +48,7 @@
 #define OG_MIXED 2
 #define OG_SPHERE 0
 #define OG_CUBE 1
+#define OG_CYLINDER 2
 
 /* ------------------------------------------------------------------------ */
 /* predicates                                                                */
@@ -70,8 +73,17 @@ double og_cube2(const double* p, const double* c) {
   return m > az ? m : az;
 }
 
+/* Vertical cylinder (the xy-only kernel of Section 2): squared horizontal
+   distance, z ignored, same evaluation order as the sphere's first terms. */
+double og_cyl2(const double* p, const double* c) {
+  double dx = p[0] - c[0];
+  double dy = p[1] - c[1];
+  return dx * dx + dy * dy;
+}
+
 static int og_inside(const double* p, const double* c, double r2, int kernel) {
   if (kernel == OG_CUBE) return og_cube2(p, c) <= r2;
+  if (kernel == OG_CYLINDER) return og_cyl2(p, c) <= r2;
   return og_d2(p, c) <= r2;
 }
 
@@ -358,7 +370,14 @@ int64_t og_kernel_search(const og_index* ix, const double* c, double r, int kern
   int64_t i0, i1, j0, j1, k0 = 0, k1 = 0;
   if (!og_axis_range(ix, 0, c[0], r, &i0, &i1)) return 0;
   if (!og_axis_range(ix, 1, c[1], r, &j0, &j1)) return 0;
-  if (ix->dim == 3 && !og_axis_range(ix, 2, c[2], r, &k0, &k1)) return 0;
+  if (ix->dim == 3) {
+    if (kernel == OG_CYLINDER) {  /* unbounded in z: every slice */
+      k0 = 0;
+      k1 = ix->nc[2] - 1;
+    } else if (!og_axis_range(ix, 2, c[2], r, &k0, &k1)) {
+      return 0;
+    }
+  }
   int64_t cnt = 0;
   for (int64_t i = i0; i <= i1; ++i)
     for (int64_t j = j0; j <= j1; ++j)

@@ -163,6 +163,35 @@ def test_lattice_sphere_and_cube_counts(dim, flavor):
     assert len(ix.kernel_search(c2, 2.0)) == expect
 
 
+@pytest.mark.parametrize("dim,flavor", [(2, 0), (3, 0), (3, 1), (3, 2)])
+def test_lattice_cylinder_counts(dim, flavor):
+    # vertical cylinder (Section 2's xy-only kernel): every z level of the
+    # lattice inside the disk x^2 + y^2 <= r^2, whatever the query's height
+    off = (508000.0, 5440000.0, 100.0)
+    xyz = cloudgen.lattice_cloud(6, offset=off)
+    ix = oracle.Index(xyz, 1.0, 1.0, dim=dim, flavor=flavor)
+    for dz in (0.0, 4.0, 40.0):  # queries above the cloud still see every level
+        c = np.array(off) + np.array([0.0, 0.0, dz])
+        for r in (1, 2, 5):
+            disk = sum(1 for x in range(-6, 7) for y in range(-6, 7) if x * x + y * y <= r * r)
+            assert len(ix.kernel_search(c, float(r), oracle.CYLINDER)) == disk * 13
+
+
+def test_cylinder_contains_sphere_and_equals_it_on_a_plane():
+    xyz = cloudgen.adversarial_cloud(3000, seed=41)
+    ix = oracle.Index(xyz, 1.0, 1.0, dim=3)
+    rng = np.random.default_rng(2)
+    for c in xyz[rng.integers(0, len(xyz), 30)]:
+        sph = set(ix.kernel_search(c, 1.3, oracle.SPHERE).tolist())
+        cyl = set(ix.kernel_search(c, 1.3, oracle.CYLINDER).tolist())
+        assert sph <= cyl
+    flat = xyz.copy()
+    flat[:, 2] = 7.25
+    ixf = oracle.Index(flat, 1.0, 1.0, dim=3)
+    for c in flat[rng.integers(0, len(flat), 30)]:
+        assert np.array_equal(ixf.kernel_search(c, 0.8, oracle.CYLINDER), ixf.kernel_search(c, 0.8, oracle.SPHERE))
+
+
 def test_lattice_knn_shells():
     off = (508000.0, 5440000.0, 100.0)
     xyz = cloudgen.lattice_cloud(4, offset=off)
@@ -203,7 +232,7 @@ def test_index_matches_brute_force(dim, flavor):
                          np.array([xyz.min(0) - 50.0])])            # far outside
     for c in qs:
         for r in (0.3, 1.0, 2.5):
-            for kern in (oracle.SPHERE, oracle.CUBE):
+            for kern in (oracle.SPHERE, oracle.CUBE, oracle.CYLINDER):
                 assert np.array_equal(ix.kernel_search(c, r, kern), oracle.brute_radius(xyz, c, r, kern))
         for k in (1, 7, 33):
             a_i, a_d = ix.knn(c[None, :], k)
