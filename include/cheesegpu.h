@@ -22,8 +22,9 @@
  *  - The neighbour sets are fixed by one predicate, evaluated in IEEE binary64
  *    with round-to-nearest and no fused multiply-add:
  *        dx = fl(p_x - c_x), dy, dz likewise;
- *        sphere: fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) <= fl(r*r)
- *        cube:   max(fl(dx*dx), fl(dy*dy), fl(dz*dz))  <= fl(r*r)
+ *        sphere:   fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) <= fl(r*r)
+ *        cube:     max(fl(dx*dx), fl(dy*dy), fl(dz*dz))  <= fl(r*r)
+ *        cylinder: fl(fl(dx*dx) + fl(dy*dy)) <= fl(r*r)   (z unbounded)
  *    (the kernels of Section 2 / Section 3.4.1 of the paper, with "<=" as in
  *    the candidate set of Section 3.4.2).  k-NN returns the first min(k, N)
  *    points under the order (sphere value d2, original id).  Both precisions
@@ -56,8 +57,9 @@ typedef enum {
    least 80 % of its voxels are non-empty, 2D = one slice (3.3.3). */
 typedef enum { CG_DENSE = 0, CG_SPARSE = 1, CG_MIXED = 2 } cg_flavor;
 
-/* Search kernels of Section 2: L2 ball and L-infinity ball (cube). */
-typedef enum { CG_SPHERE = 0, CG_CUBE = 1 } cg_kernel;
+/* Search kernels of Section 2: L2 ball, L-infinity ball (cube) and the
+   vertical cylinder (xy only: every height within the horizontal radius). */
+typedef enum { CG_SPHERE = 0, CG_CUBE = 1, CG_CYLINDER = 2 } cg_kernel;
 
 /* Storage precision of the indexed coordinates.  CG_FP64 tests every
    candidate in binary64.  CG_FP32_OFFSET stores fl32(fl64(p - O)) for a

@@ -21,7 +21,7 @@ import torch
 from . import _build
 
 DENSE, SPARSE, MIXED = 0, 1, 2
-SPHERE, CUBE = 0, 1
+SPHERE, CUBE, CYLINDER = 0, 1, 2
 FP64, FP32_OFFSET = 0, 1
 
 STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4: "CG_ERR_TIMEOUT",

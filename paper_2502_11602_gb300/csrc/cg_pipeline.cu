@@ -182,7 +182,7 @@ cg_status cg_pipeline_create(const double* xyz_dev, const int64_t* tile_offsets,
   if (dim != 2 && dim != 3) return fail(CG_ERR_INVALID, "dim must be 2 or 3");
   if (precision != CG_FP64 && precision != CG_FP32_OFFSET) return fail(CG_ERR_INVALID, "unknown precision");
   if (!(opts->radius > 0) || !isfinite(opts->radius)) return fail(CG_ERR_INVALID, "radius must be positive and finite");
-  if (opts->kernel != CG_SPHERE && opts->kernel != CG_CUBE) return fail(CG_ERR_INVALID, "unknown kernel");
+  if (opts->kernel != CG_SPHERE && opts->kernel != CG_CUBE && opts->kernel != CG_CYLINDER) return fail(CG_ERR_INVALID, "unknown kernel");
   if (opts->k < 0 || opts->k > 64) return fail(CG_ERR_INVALID, "k must be in [0, 64]");
   if (!(opts->headroom == 0 || (opts->headroom >= 1 && opts->headroom <= 16)))
     return fail(CG_ERR_INVALID, "headroom must be 0 or in [1, 16]");

@@ -66,6 +66,7 @@ __device__ __forceinline__ bool exact_inside(const double* __restrict__ p,
     double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     return d2 <= r2;
   }
+  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
   double m = fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   return m <= r2;
 }
@@ -79,6 +80,7 @@ __device__ __forceinline__ bool exact_inside4(const double4_32a& p, const double
     double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     return d2 <= r2;
   }
+  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
   double m = fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   return m <= r2;
 }
@@ -93,6 +95,9 @@ __device__ __forceinline__ int screen32(const float4& c, const float4& q, const 
   float lo, hi;
   if (KERN == CG_SPHERE) {
     v = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    lo = t.s_lo; hi = t.s_hi;
+  } else if (KERN == CG_CYLINDER) {  // two terms: the sphere's band bounds it
+    v = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
     lo = t.s_lo; hi = t.s_hi;
   } else {
     v = fmaxf(fmaxf(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -189,6 +194,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
     const int ti = ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey);
     const Tile& T = ix.tiles[ti];
     const int dim = ix.dim;
+    const int dimr = (KERN == CG_CYLINDER && dim == 3) ? 2 : dim;  // the cylinder spans every z slice
 
     for (uint32_t q0 = qb0; q0 < qb1; q0 += QB) {
       const int nqb = (int)min((uint32_t)QB, qb1 - q0);
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
           qr[t] = q;
           q_cnt[t] = 0;
           if (FILL) q_pos[t] = offsets[rec_id(q)];
-          for (int a = 0; a < dim; ++a) {
+          for (int a = 0; a < dimr; ++a) {
             float u = rec_u(q, T, a);
             float rr = __fmul_ru(__fmul_ru(thr.r_f, T.inv_sf[a]), 1.0000005f);
             float pad = __fadd_ru(__fadd_ru(rr, T.eta),
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
             hi[a] = max(hi[a], (int)floorf(uh));
           }
         }
-        for (int a = 0; a < dim; ++a) {
+        for (int a = 0; a < dimr; ++a) {
           for (int o = 16; o > 0; o >>= 1) {
             lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
             hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(RT) radius_kernel(IndexView ix, QuerySet qs,
       int lo[3], hi[3];
       bool empty = false;
       for (int a = 0; a < 3; ++a) {
-        if (a < dim) {
+        if (a < dimr) {
           lo[a] = max(s_lo[a], 0);
           hi[a] = min(s_hi[a], T.n[a] - 1);
           empty |= lo[a] > hi[a];
@@ -642,10 +648,14 @@ cudaError_t dispatch_radius(int prec, int kern, const RadiusLaunch& L, uint32_t*
   if (prec == CG_FP32_OFFSET) {
     if (kern == CG_SPHERE)
       return launch_radius<1, CG_SPHERE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+    if (kern == CG_CYLINDER)
+      return launch_radius<1, CG_CYLINDER, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
     return launch_radius<1, CG_CUBE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
   }
   if (kern == CG_SPHERE)
     return launch_radius<0, CG_SPHERE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
+  if (kern == CG_CYLINDER)
+    return launch_radius<0, CG_CYLINDER, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
   return launch_radius<0, CG_CUBE, FILL>(L, counts, offsets, out, heavy, work_ctr, status, grid, st);
 }
 
@@ -668,7 +678,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
                       cudaStream_t st) {
   if (!(r > 0) || !isfinite(r)) return fail(CG_ERR_INVALID, "radius must be positive and finite");
-  if (kernel != CG_SPHERE && kernel != CG_CUBE) return fail(CG_ERR_INVALID, "unknown kernel");
+  if (kernel != CG_SPHERE && kernel != CG_CUBE && kernel != CG_CYLINDER) return fail(CG_ERR_INVALID, "unknown kernel");
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
@@ -780,7 +790,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       if (!R.plans || !R.msize || !R.isize || !R.moff || !R.idoff || !R.big_list || !sscr)
         return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
       Lbig.qs.blk_list = R.big_list;
-      e = launch_radius_plan(ix->precision, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
+      e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
                              R.ctrs + 12, C.status, st);
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, C.status, st);
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, C.status, st);
@@ -958,7 +968,7 @@ cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, 
   H.cap = (uint32_t)std::max<int64_t>(n, 1);
   const int grid = radius_grid(ix->precision);
   const uint32_t nb = w.cap_nb;
-  e = launch_radius_plan(ix->precision, L.iv, L.qs, w.thr, w.plans, w.msize, w.isize, w.big_list, w.ctrs + 12,
+  e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.msize, w.isize, w.big_list, w.ctrs + 12,
                          ix->status, st);
   if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.msize, w.moff, nb, w.plan_scr, ix->status, st);
   if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.isize, w.idoff, nb, w.plan_scr, ix->status, st);

@@ -123,7 +123,7 @@ struct BlockPlan {
 };
 
 // Fast radius kernels (cg_radius2.cu).
-cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
+cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
                                uint32_t* big_n, const uint32_t* status, cudaStream_t st);
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,

@@ -70,6 +70,7 @@ __device__ __forceinline__ bool exact_in(const double* __restrict__ p, const dou
   double dz = __dsub_rn(__ldg(p + 2), __ldg(c + 2));
   if (KERN == CG_SPHERE)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
+  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
   return fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
 }
 template <int KERN>
@@ -77,6 +78,7 @@ __device__ __forceinline__ bool exact_in4(const double4_32a& p, const double4_32
   double dx = __dsub_rn(p.x, c.x), dy = __dsub_rn(p.y, c.y), dz = __dsub_rn(p.z, c.z);
   if (KERN == CG_SPHERE)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
+  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
   return fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
 }
 
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
                                                          uint32_t* __restrict__ msize,
                                                          uint32_t* __restrict__ isize,
                                                          uint32_t* __restrict__ big_list, uint32_t* big_n,
-                                                         const uint32_t* status) {
+                                                         const uint32_t* status, int zfull) {
   using R = typename R2<PREC>::T;
   constexpr int KW = R2<PREC>::KW;
   if (replan_pending(status)) return;
@@ -109,10 +111,11 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
     const uint32_t bkey = qs.blk_key[b];
     const Tile& T = ix.tiles[ix.ntiles == 1 ? 0 : tile_of_key(ix.tiles, ix.ntiles, bkey)];
     const int dim = ix.dim;
+    const int dimr = (zfull && dim == 3) ? 2 : dim;  // the cylinder spans every z slice
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (uint32_t t = lane; t < nq; t += 32) {
       const R q = qsrc[qb0 + t];
-      for (int a = 0; a < dim; ++a) {
+      for (int a = 0; a < dimr; ++a) {
         float u = ru(q, T, a);
         float rr = __fmul_ru(__fmul_ru(thr.r_f, T.inv_sf[a]), 1.0000005f);
         float pad = __fadd_ru(__fadd_ru(rr, T.eta), __fmul_ru(__fadd_ru(fabsf(u), rabs(q, a) * T.inv_sf[a]), 3.0e-7f));
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
     }
     bool empty = false;
     for (int a = 0; a < 3; ++a) {
-      if (a < dim) {
+      if (a < dimr) {
         for (int o = 16; o > 0; o >>= 1) {
           lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
           hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
@@ -195,24 +198,12 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
 // pairs (2p, 2p+1) as {x0, x1, y0, y1} and {z0, z1}, so that packed
 // f32x2 arithmetic evaluates two candidates per instruction; one padding pair
 // after every 16 pairs (one 32-candidate word) keeps the words on different
-// shared-memory banks.  ids are kept in a plain array.
+// shared-memory banks.
 struct PairLayout {
-  ulonglong2* xy;       // [pair_cap]
+  ulonglong2* xy;         // [pair_cap]
   unsigned long long* z;  // [pair_cap]
-  uint32_t* id;         // [KW]
 };
 __device__ __forceinline__ int pair_slot(int j) { int p = j >> 1; return p + (p >> 4); }
-
-__device__ __forceinline__ void put_pair(const PairLayout& L, int j, const float4& r) {
-  const int ps = pair_slot(j);
-  float* xy = reinterpret_cast<float*>(L.xy + ps);
-  float* z = reinterpret_cast<float*>(L.z + ps);
-  const int h = j & 1;
-  xy[h] = r.x;
-  xy[2 + h] = r.y;
-  z[h] = r.z;
-  L.id[j] = __float_as_uint(r.w);
-}
 
 // CTA-wide stable LSD radix sort of K records by id (8-bit digits, per-warp
 // ranking with match_any).  Pass p reads A (even p) or B and writes the
@@ -310,15 +301,6 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 
 template <int PREC>
 struct CountSmem;
-template <>
-struct CountSmem<1> {
-  static constexpr int KW = R2<1>::KW;
-  static constexpr int PAIRS = KW / 2 + KW / 32 + 8;
-  static constexpr size_t A = sizeof(float4) * KW;
-  static constexpr size_t Bpairs = (16 + 8) * (size_t)PAIRS + 4 * (size_t)KW;
-  static constexpr size_t Brec = sizeof(float4) * KW;
-  static constexpr size_t B = Bpairs > Brec ? Bpairs : Brec;
-};
 template <>
 struct CountSmem<0> {
   static constexpr int KW = R2<0>::KW;
@@ -419,93 +401,30 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
     for (uint32_t t = threadIdx.x; t < nq; t += CT) cnt_s[t] = 0;
     uint32_t* mb = masks + moff[b];
     const uint32_t io = idoff[b];
-    if constexpr (PREC == 1) {
-      PairLayout PL;
-      PL.xy = reinterpret_cast<ulonglong2*>(Bmem);
-      PL.z = reinterpret_cast<unsigned long long*>(Bmem + 16 * (size_t)SM::PAIRS);
-      PL.id = reinterpret_cast<uint32_t*>(Bmem + 24 * (size_t)SM::PAIRS);
-      if (K > 0)
-        cta_sort_by_id<float4, EPL>(recA, reinterpret_cast<float4*>(Bmem), (int)K, passes, hist, dbase,
-                                    [&](int pos, const float4& r) { put_pair(PL, pos, r); });
-      const float4 sent = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
-                                      __int_as_float(0x7fc00000), __uint_as_float(0xffffffffu));
-      for (uint32_t j = K + threadIdx.x; j < W * 32u; j += CT) put_pair(PL, (int)j, sent);
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < K; j += CT) ids[io + j] = PL.id[j];
-      const float slo = KERN == CG_SPHERE ? thr.s_lo : thr.c_lo;
-      const float shi = KERN == CG_SPHERE ? thr.s_hi : thr.c_hi;
-      for (uint32_t qg = 0; qg < nq; qg += CT) {
-        const uint32_t nqg = min((uint32_t)CT, nq - qg);
-        const uint32_t S = max(1u, min(W, (uint32_t)CT / nqg));
-        if (threadIdx.x < nqg * S) {
-          const uint32_t q = qg + threadIdx.x % nqg, s = threadIdx.x / nqg;
-          const float4 qq = qsrc[q0 + q];
-          const uint32_t qid = __float_as_uint(qq.w);
-          const unsigned long long QX = pk(qq.x, qq.x), QY = pk(qq.y, qq.y), QZ = pk(qq.z, qq.z);
-          uint32_t cnt = 0;
-          for (uint32_t w = s; w < W; w += S) {
-            const ulonglong2* xyw = PL.xy + w * 17u;
-            const unsigned long long* zw = PL.z + w * 17u;
-            uint32_t m_in = 0, m_hi = 0;
-#pragma unroll
-            for (int pr = 0; pr < 16; ++pr) {
-              const ulonglong2 xy = xyw[pr];
-              const unsigned long long zz = zw[pr];
-              const unsigned long long DX = sub2(xy.x, QX), DY = sub2(xy.y, QY), DZ = sub2(zz, QZ);
-              float v0, v1;
-              if (KERN == CG_SPHERE) {
-                upk(fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX))), v0, v1);
-              } else {
-                float a0, a1, b0, b1, c0, c1;
-                upk(mul2(DX, DX), a0, a1);
-                upk(mul2(DY, DY), b0, b1);
-                upk(mul2(DZ, DZ), c0, c1);
-                v0 = fmaxf(fmaxf(a0, b0), c0);
-                v1 = fmaxf(fmaxf(a1, b1), c1);
-              }
-              m_in |= (v0 <= slo ? 1u : 0u) << (2 * pr);
-              m_in |= (v1 <= slo ? 1u : 0u) << (2 * pr + 1);
-              m_hi |= (v0 <= shi ? 1u : 0u) << (2 * pr);
-              m_hi |= (v1 <= shi ? 1u : 0u) << (2 * pr + 1);
-            }
-            uint32_t band = m_hi & ~m_in;
-            while (band) {  // rare: decide in binary64 on the original coordinates
-              const int bb = __ffs(band) - 1;
-              band &= band - 1;
-              const uint32_t cid = PL.id[w * 32u + bb];
-              if (exact_in<KERN>(ix.xyz64 + 3 * (size_t)cid, q64 + 3 * (size_t)qid, thr.r2)) m_in |= 1u << bb;
-            }
-            mb[q * W + w] = m_in;
-            cnt += __popc(m_in);
-          }
-          atomicAdd(&cnt_s[q], cnt);
-        }
-      }
-    } else {
-      R* recB = reinterpret_cast<R*>(Bmem);
-      if (K > 0)
-        cta_sort_by_id<R, EPL>(recA, recB, (int)K, passes, hist, dbase,
-                               [&](int pos, const R& r) { recB[pos + (pos >> 5)] = r; });
-      for (uint32_t j = K + threadIdx.x; j < W * 32u; j += CT) recB[j + (j >> 5)] = sentinel((R*)nullptr);
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < K; j += CT) ids[io + j] = rid(recB[j + (j >> 5)]);
-      for (uint32_t qg = 0; qg < nq; qg += CT) {
-        const uint32_t nqg = min((uint32_t)CT, nq - qg);
-        const uint32_t S = max(1u, min(W, (uint32_t)CT / nqg));
-        if (threadIdx.x < nqg * S) {
-          const uint32_t q = qg + threadIdx.x % nqg, s = threadIdx.x / nqg;
-          const R qq = qsrc[q0 + q];
-          uint32_t cnt = 0;
-          for (uint32_t w = s; w < W; w += S) {
-            const R* base = recB + w * 33u;
-            uint32_t m_in = 0;
+    // binary64 records: the exact predicate directly
+    R* recB = reinterpret_cast<R*>(Bmem);
+    if (K > 0)
+      cta_sort_by_id<R, EPL>(recA, recB, (int)K, passes, hist, dbase,
+                             [&](int pos, const R& r) { recB[pos + (pos >> 5)] = r; });
+    for (uint32_t j = K + threadIdx.x; j < W * 32u; j += CT) recB[j + (j >> 5)] = sentinel((R*)nullptr);
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < K; j += CT) ids[io + j] = rid(recB[j + (j >> 5)]);
+    for (uint32_t qg = 0; qg < nq; qg += CT) {
+      const uint32_t nqg = min((uint32_t)CT, nq - qg);
+      const uint32_t S = max(1u, min(W, (uint32_t)CT / nqg));
+      if (threadIdx.x < nqg * S) {
+        const uint32_t q = qg + threadIdx.x % nqg, s = threadIdx.x / nqg;
+        const R qq = qsrc[q0 + q];
+        uint32_t cnt = 0;
+        for (uint32_t w = s; w < W; w += S) {
+          const R* base = recB + w * 33u;
+          uint32_t m_in = 0;
 #pragma unroll 8
-            for (int bb = 0; bb < 32; ++bb) m_in |= (exact_in4<KERN>(base[bb], qq, thr.r2) ? 1u : 0u) << bb;
-            mb[q * W + w] = m_in;
-            cnt += __popc(m_in);
-          }
-          atomicAdd(&cnt_s[q], cnt);
+          for (int bb = 0; bb < 32; ++bb) m_in |= (exact_in4<KERN>(base[bb], qq, thr.r2) ? 1u : 0u) << bb;
+          mb[q * W + w] = m_in;
+          cnt += __popc(m_in);
         }
+        atomicAdd(&cnt_s[q], cnt);
       }
     }
     __syncthreads();
@@ -551,6 +470,8 @@ __device__ __forceinline__ void pair_test(const ulonglong2& xy, unsigned long lo
   const unsigned long long DX = sub2(xy.x, QX), DY = sub2(xy.y, QY), DZ = sub2(zz, QZ);
   if (KERN == CG_SPHERE) {
     upk(fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX))), v0, v1);
+  } else if (KERN == CG_CYLINDER) {
+    upk(fma2(DY, DY, mul2(DX, DX)), v0, v1);
   } else {
     float a0, a1, b0, b1, c0, c1;
     upk(mul2(DX, DX), a0, a1);
@@ -605,8 +526,10 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   const uint32_t* __restrict__ sid = ix.sid;
   const float4* __restrict__ qsrc = qs.all_points ? pts : qs.qrec;
   const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
-  const float slo = KERN == CG_SPHERE ? thr.s_lo : thr.c_lo;
-  const float shi = KERN == CG_SPHERE ? thr.s_hi : thr.c_hi;
+  // the cylinder's two-term value has a smaller error than the sphere's
+  // three-term one: the sphere's band bounds it
+  const float slo = KERN == CG_CUBE ? thr.c_lo : thr.s_lo;
+  const float shi = KERN == CG_CUBE ? thr.c_hi : thr.s_hi;
   const float far = __int_as_float(0x7f000000);  // padding candidate: its square overflows to +inf
   for (;;) {
     if (tis == 0) sbox[0] = atomicAdd(work, 1u);
@@ -1039,15 +962,16 @@ int resident_grid(F kern, int threads, size_t smem) {
 
 // ------------------------------------------------------------------ host
 
-cudaError_t launch_radius_plan(int prec, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
+cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
                                uint32_t* big_n, const uint32_t* status, cudaStream_t st) {
+  const int zfull = kern == CG_CYLINDER ? 1 : 0;
   const int grid = (int)std::min<int64_t>((qs.nblocks + 3) / 4 + 1, (int64_t)sm_count() * 16);
   ProfScope prof("radius_plan", st);
   if (prec == CG_FP32_OFFSET)
-    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status);
+    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull);
   else
-    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status);
+    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull);
   note_launch();
   return cudaGetLastError();
 }
@@ -1069,11 +993,10 @@ cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const 
     kfn<<<resident_grid(kfn, CT, smem), CT, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, \
                                                         masks, ids, work, status, passes);       \
   } while (0)
-  if (prec == CG_FP32_OFFSET) {
-    if (kern == CG_SPHERE) CG_LAUNCH_C2(1, CG_SPHERE); else CG_LAUNCH_C2(1, CG_CUBE);
-  } else {
-    if (kern == CG_SPHERE) CG_LAUNCH_C2(0, CG_SPHERE); else CG_LAUNCH_C2(0, CG_CUBE);
-  }
+  (void)prec;  // binary64 records only (binary32 records use the warp-per-group kernels)
+  if (kern == CG_SPHERE) CG_LAUNCH_C2(0, CG_SPHERE);
+  else if (kern == CG_CYLINDER) CG_LAUNCH_C2(0, CG_CYLINDER);
+  else CG_LAUNCH_C2(0, CG_CUBE);
 #undef CG_LAUNCH_C2
   note_launch();
   return cudaGetLastError();
@@ -1084,13 +1007,9 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                 const uint32_t* status, cudaStream_t st) {
   ProfScope prof("radius_fill2", st);
-  if (prec == CG_FP32_OFFSET) {
-    auto kfn = radius_fill2_kernel<1>;
-    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
-  } else {
-    auto kfn = radius_fill2_kernel<0>;
-    kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
-  }
+  (void)prec;  // binary64 records only
+  auto kfn = radius_fill2_kernel<0>;
+  kfn<<<resident_grid(kfn, CT, 0), CT, 0, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, work, status);
   note_launch();
   return cudaGetLastError();
 }
@@ -1118,6 +1037,10 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
     CG_C5(CG_SPHERE, 512, 4, 1, 0u, work);
     CG_C5(CG_SPHERE, 1024, 4, 2, 1u, work + 1);
     CG_C5(CG_SPHERE, 2048, 4, 4, 2u, work + 2);
+  } else if (kern == CG_CYLINDER) {
+    CG_C5(CG_CYLINDER, 512, 4, 1, 0u, work);
+    CG_C5(CG_CYLINDER, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_CYLINDER, 2048, 4, 4, 2u, work + 2);
   } else {
     CG_C5(CG_CUBE, 512, 4, 1, 0u, work);
     CG_C5(CG_CUBE, 1024, 4, 2, 1u, work + 1);

@@ -307,7 +307,7 @@ cg_status cg_server_submit(cg_server_t s, const cg_request_t* req, int64_t* id_o
   if (ix->ntiles != 1) return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
   if (req->op == CG_REQ_RADIUS) {
     if (!(req->radius > 0) || !isfinite(req->radius)) return fail(CG_ERR_INVALID, "radius must be positive and finite");
-    if (req->kernel != CG_SPHERE && req->kernel != CG_CUBE) return fail(CG_ERR_INVALID, "unknown kernel");
+    if (req->kernel != CG_SPHERE && req->kernel != CG_CUBE && req->kernel != CG_CYLINDER) return fail(CG_ERR_INVALID, "unknown kernel");
   } else if (req->op == CG_REQ_KNN) {
     if (req->k < 1 || req->k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
   } else {

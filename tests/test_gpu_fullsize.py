@@ -87,6 +87,11 @@ def test_tls_20m_3d_radii_and_knn(tls, flavor):
         o_off, o_ind = ref.radius_search(q_all[sel], r, threads=16)
         assert np.array_equal(off.cpu().numpy(), o_off), f"r={r} counts"
         assert np.array_equal(ind.cpu().numpy(), o_ind), f"r={r} indices"
+    # the vertical cylinder spans every z slice of the 3D grid's columns
+    sel = rng.integers(0, len(q_all), 5_000)
+    off, ind = ix.radius_search(qd[torch.from_numpy(sel).to(DEV)].contiguous(), 0.05, cg.CYLINDER)
+    o_off, o_ind = ref.radius_search(q_all[sel], 0.05, oracle.CYLINDER, threads=16)
+    assert np.array_equal(off.cpu().numpy(), o_off) and np.array_equal(ind.cpu().numpy(), o_ind), "cylinder"
     idx, d2 = ix.knn(qd, 16)
     rows = rng.integers(0, len(q_all), 5000)
     r_idx, r_d2 = ref.knn(q_all[rows], 16, threads=16)

@@ -194,3 +194,18 @@ def test_query_buffer_rewritten_in_place_is_planned_again():
         r_idx, r_d2 = ref.knn(qh, 8, threads=8)
         assert np.array_equal(idx.cpu().numpy(), r_idx) and np.array_equal(d2.cpu().numpy(), r_d2)
     ix.close()
+
+
+@pytest.mark.parametrize("prec", [cg.FP32_OFFSET, cg.FP64])
+@pytest.mark.parametrize("dim,flavor", [(2, cg.DENSE), (3, cg.DENSE), (3, cg.SPARSE), (3, cg.MIXED)])
+def test_cylinder_kernel(prec, dim, flavor):
+    # vertical cylinder: every height within the horizontal radius (on a 3D
+    # grid every z slice of the voxel columns is searched)
+    xyz = cloudgen.als_uniform(20_000, extent=(30.0, 30.0), seed=14)
+    rng = np.random.default_rng(6)
+    poles = np.stack([rng.uniform(0, 30, 4000), rng.uniform(0, 30, 4000), rng.uniform(-3, 25, 4000)], 1)
+    xyz = np.ascontiguousarray(np.concatenate([xyz, poles + xyz.min(0) * [1, 1, 0]]))
+    for r in (0.4, 1.0, 2.2):
+        _check(xyz, None, r, 1.0, 0.5, dim=dim, flavor=flavor, prec=prec, kernel=cg.CYLINDER)
+    q = xyz[rng.integers(0, len(xyz), 500)] + rng.normal(0, 2.0, (500, 3))
+    _check(xyz, q, 1.5, 1.0, 0.5, dim=dim, flavor=flavor, prec=prec, kernel=cg.CYLINDER)
