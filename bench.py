@@ -651,6 +651,91 @@ def run_serving(args):
         dist.destroy_process_group()
 
 
+def run_latency(args):
+    """Per-call latency of small query batches through the public API (the
+    paper times single random queries): batches of 1 .. 100k random queries
+    drawn near the 12M tile's points, sphere r = 1 m (count + fill) and
+    k-NN k = 16, median over repetitions, per call and per query."""
+    import numpy as np
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    xyz = cloudgen.als_urban(args.points)
+    ix = cg.Index(torch.from_numpy(xyz).to(dev), CELL)
+    rng = np.random.default_rng(11)
+    rows = []
+    for B in (1, 10, 100, 1000, 10_000, 100_000):
+        reps = 50 if B <= 1000 else 10
+        qs = [torch.from_numpy(np.ascontiguousarray(
+            xyz[rng.integers(0, len(xyz), B)] + rng.normal(0, 0.5, (B, 3)))).to(dev) for _ in range(reps + 3)]
+        torch.cuda.synchronize()
+        out = {}
+        for kind in ("radius", "knn"):
+            ts = []
+            for i, q in enumerate(qs):
+                t0 = time.perf_counter()
+                if kind == "radius":
+                    off, ind = ix.radius_search(q, RADIUS, check=False)
+                else:
+                    idx, d2 = ix.knn(q, 16, check=False)
+                torch.cuda.synchronize()
+                if i >= 3:
+                    ts.append(time.perf_counter() - t0)
+            med = statistics.median(ts)
+            out[kind] = {"us_per_call": med * 1e6, "us_per_query": med * 1e6 / B, "queries_per_s": B / med}
+        rows.append({"batch": B, **out})
+    ix.close()
+    line = {"metric": "query latency through the public API (12M ALS tile, sphere r=1 m, k-NN k=16)",
+            "value": rows[0]["radius"]["us_per_call"], "unit": "us per single-query call", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "12M ALS tile, 2D dense 1 m; random queries within 0.5 m of the points; "
+                                   "host-timed, synchronised, median of 10-50 calls per batch size"},
+            "batches": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_memory(args):
+    """Device memory of the index per flavour, dimension and cell size on the
+    12M tile, against the 8 n bytes (one pointer per point) the paper takes
+    as the minimum of a point index."""
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    xyz = cloudgen.als_urban(args.points)
+    n = len(xyz)
+    x = torch.from_numpy(xyz).to(dev)
+    rows = []
+    names = {cg.DENSE: "dense", cg.SPARSE: "sparse", cg.MIXED: "mixed"}
+    for dim in (2, 3):
+        for cell in (0.5, 1.0, 2.0):
+            for fl in (cg.DENSE, cg.SPARSE, cg.MIXED):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ix = cg.Index(x, cell, cell, dim=dim, flavor=fl)
+                torch.cuda.synchronize()
+                t_build = time.perf_counter() - t0
+                info = ix.info()
+                # records (16 n) + exact copy (24 n) are point data; the rest indexes them
+                tables = info["device_bytes"] - 40 * n
+                rows.append({"dim": dim, "cell_m": cell, "flavor": names[fl], "ncell": info["ncell"],
+                             "nonempty": info["nonempty"], "device_MiB": info["device_bytes"] / 2 ** 20,
+                             "index_MiB": tables / 2 ** 20, "index_over_8n": tables / (8.0 * n),
+                             "build_ms": t_build * 1e3})
+                ix.close()
+    line = {"metric": "index device memory vs the 8 n-byte minimum (12M ALS tile)", "value": None,
+            "unit": "MiB", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "12M ALS tile; index bytes = device bytes minus the 16 n B binary32 records "
+                                   "and the 24 n B exact copy", "n_points": n, "min_8n_MiB": 8 * n / 2 ** 20},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -663,7 +748,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS, help="tile size (profiling cases only)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison on the tile")
-    ap.add_argument("--workload", choices=["tile", "batched", "serving"], default="tile")
+    ap.add_argument("--workload", choices=["tile", "batched", "serving", "latency", "memory"], default="tile")
     ap.add_argument("--tiles", type=int, default=256)
     ap.add_argument("--batch-points", type=int, default=60_000_000)
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -680,6 +765,10 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "latency":
+        run_latency(args)
+    elif args.workload == "memory":
+        run_memory(args)
     else:
         run_ours(args)
 
