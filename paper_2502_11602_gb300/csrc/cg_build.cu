@@ -348,7 +348,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   unsigned long long* bb;
   CG_ALLOC(toff_dev, int64_t, ntiles + 1, tmp);
   CG_ALLOC(bb, unsigned long long, 6 * ntiles, tmp);
-  CG_CUDA(cudaMemcpyAsync(toff_dev, toff_host, sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
+  CG_CUDA(host_put(toff_dev, toff_host, sizeof(int64_t) * (ntiles + 1), st));
   bbox_init_kernel<<<(6 * ntiles + 255) / 256, 256, 0, st>>>(bb, ntiles); note_launch();
   {
     ProfScope prof("build_bbox", st);
@@ -358,9 +358,10 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_CUDA(cudaGetLastError());
   std::vector<unsigned long long> bbh(6 * ntiles);
   uint32_t st_word = 0;
-  CG_CUDA(cudaMemcpyAsync(bbh.data(), bb, 8 * 6 * ntiles, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(&st_word, ix->status, 4, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
+  HostRead rd;
+  rd.get(bbh.data(), bb, 8 * 6 * ntiles);
+  rd.get(&st_word, ix->status, 4);
+  CG_CUDA(rd.sync(st));
   if (st_word & ST_NONFINITE) return bail(CG_ERR_INVALID, "non-finite point coordinate");
 
   // grid of every tile (host, binary64; Eq. grid-size)
@@ -411,8 +412,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   ix->nslices = (int64_t)slice_base;
   ix->enc_err0 = ix->tiles_host[0].enc_err;
   CG_ALLOC(ix->tiles, Tile, ntiles, ix->bufs);
-  CG_CUDA(cudaMemcpyAsync(ix->tiles, ix->tiles_host.data(), sizeof(Tile) * ntiles,
-                          cudaMemcpyHostToDevice, st));
+  CG_CUDA(host_put(ix->tiles, ix->tiles_host.data(), sizeof(Tile) * ntiles, st));
 
   // B1: keys
   uint32_t *keys, *skeys, *perm;
@@ -438,7 +438,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
 
   // B4: records and the exact binary64 copy in original order
   CG_ALLOC(ix->xyz64, double, 3 * n, ix->bufs);
-  CG_CUDA(cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(dev_copy(ix->xyz64, xyz, sizeof(double) * 3 * n, st));
   if (precision == CG_FP32_OFFSET) CG_ALLOC(ix->pts32, float4, n, ix->bufs);
   else CG_ALLOC(ix->pts64s, double4_32a, n, ix->bufs);
   {
@@ -460,8 +460,8 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
     CG_CUDA(exclusive_scan_u32_u32(flag, rank, n, scan_scratch, ix->status, st));
   }
   uint32_t m = 0;
-  CG_CUDA(cudaMemcpyAsync(&m, rank + n, 4, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
+  rd.get(&m, rank + n, 4);
+  CG_CUDA(rd.sync(st));
   ix->nkeys = m;
   CG_ALLOC(ix->ukeys, uint32_t, m, ix->bufs);
   CG_ALLOC(ix->ustart, uint32_t, m + 1, ix->bufs);
@@ -493,8 +493,8 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
       CG_CUDA(cudaMemsetAsync(ne, 0, 4 * slice_base, st));
       slice_count_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, m, ix->tiles, ntiles, dim, ne); note_launch();
       std::vector<uint32_t> neh(slice_base);
-      CG_CUDA(cudaMemcpyAsync(neh.data(), ne, 4 * slice_base, cudaMemcpyDeviceToHost, st));
-      CG_CUDA(cudaStreamSynchronize(st));
+      rd.get(neh.data(), ne, 4 * slice_base);
+      CG_CUDA(rd.sync(st));
       std::vector<uint8_t> dense(slice_base);
       std::vector<uint32_t> off(slice_base);
       uint64_t tab = 0;
@@ -512,8 +512,8 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
       CG_ALLOC(ix->slice_dense, uint8_t, slice_base, ix->bufs);
       CG_ALLOC(ix->slice_tab_off, uint32_t, slice_base, ix->bufs);
       CG_ALLOC(ix->mtab, uint2, std::max<uint64_t>(tab, 1), ix->bufs);
-      CG_CUDA(cudaMemcpyAsync(ix->slice_dense, dense.data(), slice_base, cudaMemcpyHostToDevice, st));
-      CG_CUDA(cudaMemcpyAsync(ix->slice_tab_off, off.data(), 4 * slice_base, cudaMemcpyHostToDevice, st));
+      CG_CUDA(host_put(ix->slice_dense, dense.data(), slice_base, st));
+      CG_CUDA(host_put(ix->slice_tab_off, off.data(), 4 * slice_base, st));
       CG_CUDA(cudaMemsetAsync(ix->mtab, 0, 8 * std::max<uint64_t>(tab, 1), st));
       mixed_fill_kernel<<<grid_for(m, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, m, ix->tiles,
                                                                     ntiles, dim, ix->slice_dense,
@@ -522,10 +522,10 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
     }
   }
   uint32_t maxrun = 0;
-  CG_CUDA(cudaMemcpyAsync(&maxrun, ix->scratch_u32, 4, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(&st_word, ix->status, 4, cudaMemcpyDeviceToHost, st));
+  rd.get(&maxrun, ix->scratch_u32, 4);
+  rd.get(&st_word, ix->status, 4);
   tmp.release(st);
-  CG_CUDA(cudaStreamSynchronize(st));
+  CG_CUDA(rd.sync(st));
   ix->max_pts_per_voxel = (int)maxrun;
   if (st_word & ST_TIMEOUT) return bail(CG_ERR_TIMEOUT, "device wait bound reached during build");
   if (st_word & ST_INTERNAL) return bail(CG_ERR_INTERNAL, "hash table insertion failed");
@@ -560,7 +560,7 @@ cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st) {
   std::vector<int64_t> toff(ix->ntiles + 1);
   for (int t = 0; t < ix->ntiles; ++t) toff[t] = ix->tiles_host[t].pt_base;
   toff[ix->ntiles] = n;
-  cudaError_t e = cudaMemcpyAsync(w.toff, toff.data(), 8 * toff.size(), cudaMemcpyHostToDevice, st);
+  cudaError_t e = host_put(w.toff, toff.data(), 8 * toff.size(), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "pipeline build work");
   int bits = 0;
@@ -592,7 +592,7 @@ cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream
   gather_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->sid, w.skeys, ix->tiles, T, ix->pts32,
                                                              ix->pts64s); note_launch();
   if (ix->xyz64 != xyz) {  // a pipeline reads the caller's buffer in place
-    e = cudaMemcpyAsync(ix->xyz64, xyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st);
+    e = dev_copy(ix->xyz64, xyz, sizeof(double) * 3 * n, st);
     if (e != cudaSuccess) return cuda_fail(e, "replay copy");
   }
   run_flag_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag); note_launch();

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -163,6 +164,185 @@ ProfScope::~ProfScope() {
 
 void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// ---------------------------------------------------------------------------
+// Copy-engine-free small transfers (HostRead, host_put, dev_copy)
+// ---------------------------------------------------------------------------
+namespace {
+struct XferItem {
+  const void* src;
+  void* dst;
+  unsigned long long bytes;
+};
+constexpr int kXferItems = 8;
+struct XferBatch {
+  XferItem it[kXferItems];
+  int n;
+};
+
+// Every item is copied by the whole grid, in 16-, 8-, 4- or 1-byte units as
+// the alignment of both ends and of the length allows.
+__global__ void __launch_bounds__(256) xfer_kernel(XferBatch b) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int i = 0; i < b.n; ++i) {
+    const XferItem x = b.it[i];
+    const uintptr_t a = (uintptr_t)x.src | (uintptr_t)x.dst | (uintptr_t)x.bytes;
+    if ((a & 15) == 0) {
+      const uint4* s = (const uint4*)x.src;
+      uint4* d = (uint4*)x.dst;
+      for (size_t w = t; w < x.bytes / 16; w += stride) d[w] = s[w];
+    } else if ((a & 7) == 0) {
+      const uint2* s = (const uint2*)x.src;
+      uint2* d = (uint2*)x.dst;
+      for (size_t w = t; w < x.bytes / 8; w += stride) d[w] = s[w];
+    } else if ((a & 3) == 0) {
+      const uint32_t* s = (const uint32_t*)x.src;
+      uint32_t* d = (uint32_t*)x.dst;
+      for (size_t w = t; w < x.bytes / 4; w += stride) d[w] = s[w];
+    } else {
+      const unsigned char* s = (const unsigned char*)x.src;
+      unsigned char* d = (unsigned char*)x.dst;
+      for (size_t w = t; w < x.bytes; w += stride) d[w] = s[w];
+    }
+  }
+}
+
+cudaError_t launch_xfer(const XferBatch& b, size_t max_bytes, int max_blocks, cudaStream_t st) {
+  if (b.n == 0) return cudaSuccess;
+  size_t units = (max_bytes + 15) / 16;
+  int blocks = (int)std::min<size_t>((units + 255) / 256, (size_t)max_blocks);
+  xfer_kernel<<<std::max(blocks, 1), 256, 0, st>>>(b);
+  note_launch();
+  return cudaGetLastError();
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Mapped pinned host buffer of one host thread; `done` marks the last
+// kernel that used it.
+struct Mapped {
+  char* p = nullptr;   // host address
+  char* dp = nullptr;  // the same bytes as the device addresses them
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  ~Mapped() {
+    if (pending) cudaEventSynchronize(done);
+    if (p) cudaFreeHost(p);
+    if (done) cudaEventDestroy(done);
+    cudaGetLastError();
+  }
+  // waits for the buffer's last user, then grows it to `bytes` if needed
+  cudaError_t take(size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    if (!done && (e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if (pending && (e = cudaEventSynchronize(done)) != cudaSuccess) return e;
+    pending = false;
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = dp = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 64 << 10);
+    if ((e = cudaHostAlloc((void**)&p, want, cudaHostAllocMapped | cudaHostAllocPortable)) != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    if ((e = cudaHostGetDevicePointer((void**)&dp, p, 0)) != cudaSuccess) {
+      cudaFreeHost(p);
+      p = dp = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  cudaError_t used_on(cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(done, st);
+    pending = e == cudaSuccess;
+    return e;
+  }
+};
+// Reads and puts use separate buffers; puts rotate over a few so that a
+// put seldom waits for the previous one's kernel.
+thread_local Mapped t_read;
+thread_local Mapped t_put[4];
+thread_local unsigned t_put_next = 0;
+
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+}  // namespace
+
+void HostRead::get(void* host, const void* dev, size_t bytes) {
+  if (n_ < kMax) {
+    host_[n_] = host;
+    dev_[n_] = dev;
+    bytes_[n_] = bytes;
+  }
+  ++n_;
+}
+
+cudaError_t HostRead::sync(cudaStream_t st) {
+  int n = n_;
+  n_ = 0;
+  if (n > kMax) return cudaErrorInvalidValue;
+  if (capturing(st)) return cudaErrorStreamCaptureUnsupported;
+  size_t total = 0, most = 0;
+  for (int i = 0; i < n; ++i) {
+    total += align16(bytes_[i]);
+    most = std::max(most, bytes_[i]);
+  }
+  cudaError_t e = t_read.take(total);
+  if (e != cudaSuccess) return e;
+  XferBatch b{};
+  b.n = n;
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    b.it[i] = {dev_[i], t_read.dp + off, bytes_[i]};
+    off += align16(bytes_[i]);
+  }
+  if ((e = launch_xfer(b, most, 64, st)) != cudaSuccess) return e;
+  if ((e = t_read.used_on(st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  t_read.pending = false;
+  off = 0;
+  for (int i = 0; i < n; ++i) {
+    memcpy(host_[i], t_read.p + off, bytes_[i]);
+    off += align16(bytes_[i]);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t host_put(void* dev, const void* host, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (capturing(st)) return cudaErrorStreamCaptureUnsupported;
+  Mapped& m = t_put[t_put_next++ % 4];
+  cudaError_t e = m.take(bytes);
+  if (e != cudaSuccess) return e;
+  memcpy(m.p, host, bytes);
+  XferBatch b{};
+  b.n = 1;
+  b.it[0] = {m.dp, dev, bytes};
+  if ((e = launch_xfer(b, bytes, 64, st)) != cudaSuccess) return e;
+  return m.used_on(st);
+}
+
+cudaError_t dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  XferBatch b{};
+  b.n = 1;
+  b.it[0] = {src, dst, bytes};
+  int sms = 152;
+  int d = 0;
+  if (cudaGetDevice(&d) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+  cudaGetLastError();
+  return launch_xfer(b, bytes, 8 * sms, st);
+}
+
 cg_status fail(cg_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
@@ -216,9 +396,14 @@ cg_status check_status(cg_index* ix, cudaStream_t st) { return check_status_word
 
 cg_status check_status_word(uint32_t* status, cudaStream_t st) {
   uint32_t w = 0;
-  cudaError_t e = cudaMemcpyAsync(&w, status, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  HostRead rd;
+  rd.get(&w, status, 4);
+  cudaError_t e = rd.sync(st);
   if (e != cudaSuccess) return cuda_fail(e, "status readback");
+  return status_verdict(w, status, st);
+}
+
+cg_status status_verdict(uint32_t w, uint32_t* status, cudaStream_t st) {
   if (w & (ST_NONFINITE | ST_TIMEOUT | ST_OVERFLOW | ST_INTERNAL)) {
     cudaMemsetAsync(status, 0, 4, st);
     if (w & ST_NONFINITE) return fail(CG_ERR_INVALID, "non-finite query coordinate");

@@ -191,6 +191,9 @@ namespace cg {
 // Reads and clears the device status word (synchronises the stream).
 cg_status check_status(cg_index* ix, cudaStream_t st);
 cg_status check_status_word(uint32_t* status, cudaStream_t st);
+// The error a status word `w` already read back stands for (clears the
+// device word on an error).
+cg_status status_verdict(uint32_t w, uint32_t* status, cudaStream_t st);
 cg_status prepare_queries(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, bool reuse, cudaStream_t st);
 cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,

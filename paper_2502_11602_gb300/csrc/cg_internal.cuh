@@ -54,10 +54,6 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 // Counts kernel launches made by the library (host side, diagnostics).
 void note_launch(int n = 1);
 
-// Device-time tracing of the library's kernels (off unless enabled through
-// cg_profile_enable): a scope records CUDA events around the launches it
-// encloses on their stream; nothing is recorded while a stream is being
-// captured into a graph.
 // Fork / join of independent kernels of one pass onto extra streams (one
 // set per host thread and device), so that they overlap on the GPU: every
 // branch starts after the work already on the origin stream, and the origin
@@ -81,6 +77,10 @@ struct Fork {
   bool joined_ = false;
 };
 
+// Device-time tracing of the library's kernels (off unless enabled through
+// cg_profile_enable): a scope records CUDA events around the launches it
+// encloses on their stream; nothing is recorded while a stream is being
+// captured into a graph.
 struct ProfScope {
   ProfScope(const char* name, cudaStream_t st);
   ~ProfScope();
@@ -90,6 +90,38 @@ struct ProfScope {
   cudaStream_t st = nullptr;
   cudaEvent_t a = nullptr;
 };
+
+// Small host <-> device transfers that do not use the copy engines.  A copy
+// engine serves its queue in order, so a 4-byte cudaMemcpyAsync readback
+// issued on one stream waits behind every bulk copy in the same direction
+// that any stream of the process has in flight (a 2.7 GB result download
+// holds it ~14 ms).  Here a kernel moves the bytes through mapped pinned
+// host memory, which the SMs reach directly; the staging buffers belong to
+// the calling host thread.
+//
+// HostRead: queue device -> host reads with get(); sync() launches one
+// copy kernel for all of them on `st`, synchronizes `st` and stores the
+// bytes at the host addresses.  Not usable while `st` is being captured.
+class HostRead {
+ public:
+  void get(void* host, const void* dev, size_t bytes);
+  cudaError_t sync(cudaStream_t st);
+
+ private:
+  static constexpr int kMax = 8;
+  void* host_[kMax];
+  const void* dev_[kMax];
+  size_t bytes_[kMax];
+  int n_ = 0;
+};
+
+// Host -> device: stages `bytes` from `host` and copies them into `dev` on
+// `st` with a kernel.  `host` may be reused on return; the copy is ordered
+// on `st` like a cudaMemcpyAsync.  Not usable while `st` is being captured.
+cudaError_t host_put(void* dev, const void* host, size_t bytes, cudaStream_t st);
+
+// Device -> device copy by a kernel on `st` (HBM bandwidth, no copy engine).
+cudaError_t dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -1025,8 +1025,9 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   } else {
     QueryPlan& P = C.plan;
     if (P.nblocks_host_version != P.version) {
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&P.nblocks, P.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      HostRead rd;
+      rd.get(&P.nblocks, P.nblocks_dev, 4);
+      if (e == cudaSuccess) e = rd.sync(st);
       P.nblocks_host_version = P.version;
     }
     qs.all_points = 0;

@@ -151,11 +151,14 @@ cg_status launch(cg_pipeline* p, cudaStream_t st) {
   return CG_OK;
 }
 
-// Synchronises, reads and clears the status word.
-cg_status read_status(cg_pipeline* p, cudaStream_t st, uint32_t* word) {
-  cudaError_t e = cudaMemcpyAsync(word, p->ix->status, 4, cudaMemcpyDeviceToHost, st);
+// Synchronises, reads and clears the status word; with `total`, also reads
+// the CSR total of the run in the same transfer.
+cg_status read_status(cg_pipeline* p, cudaStream_t st, uint32_t* word, int64_t* total = nullptr) {
+  HostRead rd;
+  rd.get(word, p->ix->status, 4);
+  if (total) rd.get(total, p->offsets + p->toff.back(), 8);
+  cudaError_t e = rd.sync(st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->ix->status, 0, 4, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "pipeline status");
   return CG_OK;
 }
@@ -228,7 +231,7 @@ cg_status cg_pipeline_run(cg_pipeline_t p, void* stream, int64_t* total_host) {
   cg_status s = launch(p, st);
   if (s != CG_OK || !total_host) return s;
   uint32_t w = 0;
-  s = read_status(p, st, &w);
+  s = read_status(p, st, &w, total_host);
   if (s != CG_OK) return s;
   if (w & ST_REPLAN) {
     // new data outgrew the plan: plan again from the current coordinates
@@ -237,17 +240,11 @@ cg_status cg_pipeline_run(cg_pipeline_t p, void* stream, int64_t* total_host) {
     s = setup(p, st);
     if (s != CG_OK) return s;
     s = launch(p, st);
-    if (s == CG_OK) s = read_status(p, st, &w);
+    if (s == CG_OK) s = read_status(p, st, &w, total_host);
     if (s != CG_OK) return s;
     if (w & ST_REPLAN) return fail(CG_ERR_INTERNAL, "pipeline re-plan did not fit its own data");
   }
-  s = status_error(w);
-  if (s != CG_OK) return s;
-  const int64_t n = p->toff.back();
-  cudaError_t e = cudaMemcpyAsync(total_host, p->offsets + n, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "pipeline total");
-  return CG_OK;
+  return status_error(w);
 }
 
 cg_status cg_pipeline_outputs(cg_pipeline_t p, int64_t** offsets, int32_t** indices, int32_t** knn_idx,

@@ -712,7 +712,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
     for (const Tile& T : ix->tiles_host) emax = std::max(emax, (double)T.enc_err);
     if (all_points) {
       Thresholds th = make_thresholds(r, emax, emax);
-      e = cudaMemcpyAsync(R.thr, &th, sizeof th, cudaMemcpyHostToDevice, st);
+      e = host_put(R.thr, &th, sizeof th, st);
       static_assert(sizeof(th) <= sizeof(R.thr_host), "threshold copy");
       memcpy(R.thr_host, &th, sizeof th);
     } else {
@@ -765,8 +765,9 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
     // the block count lives on the device: copy it into the launch struct
     // through a tiny synchronous read only once per plan
     if (C.plan.nblocks_host_version != C.plan.version) {
-      e = cudaMemcpyAsync(&C.plan.nblocks, C.plan.nblocks_dev, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      HostRead rd;
+      rd.get(&C.plan.nblocks, C.plan.nblocks_dev, 4);
+      e = rd.sync(st);
       if (e != cudaSuccess) return cuda_fail(e, "query plan readback");
       C.plan.nblocks_host_version = C.plan.version;
     }
@@ -795,10 +796,11 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, C.status, st);
       if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, C.status, st);
       uint32_t tots[3] = {0, 0, 0};
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[0], R.moff + nb, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[1], R.idoff + nb, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&tots[2], R.ctrs + 12, 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      HostRead rd;
+      rd.get(&tots[0], R.moff + nb, 4);
+      rd.get(&tots[1], R.idoff + nb, 4);
+      rd.get(&tots[2], R.ctrs + 12, 4);
+      if (e == cudaSuccess) e = rd.sync(st);
       if (e != cudaSuccess) return cuda_fail(e, "radius plan");
       R.masks = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[0], 1), st);
       R.ids = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[1], 1), st);
@@ -852,14 +854,17 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
     if (e != cudaSuccess) return cuda_fail(e, "offsets scan");
     uint32_t stats[4] = {0, 0, 0, 0};
     if (total_host) {
-      e = cudaMemcpyAsync(total_host, offsets + nqq, 8, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(stats, R.ctrs, 16, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      uint32_t w = 0;
+      HostRead rd;
+      rd.get(total_host, offsets + nqq, 8);
+      rd.get(stats, R.ctrs, 16);
+      rd.get(&w, C.status, 4);
+      e = rd.sync(st);
       if (e != cudaSuccess) return cuda_fail(e, "count readback");
       R.heavy_count = stats[0];
       R.heavy_scratch = ((uint64_t)stats[3] << 32) | stats[2];
       R.stats_known = true;
-      cg_status s = check_status_word(C.status, st);
+      cg_status s = status_verdict(w, C.status, st);
       if (s != CG_OK) return s;
     } else {
       R.stats_known = false;
@@ -870,8 +875,9 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
   // fill: sort the rows that were assembled from several runs
   if (!R.stats_known) {
     uint32_t stats[4] = {0, 0, 0, 0};
-    e = cudaMemcpyAsync(stats, R.ctrs, 16, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    HostRead rd;
+    rd.get(stats, R.ctrs, 16);
+    e = rd.sync(st);
     if (e != cudaSuccess) return cuda_fail(e, "heavy readback");
     R.heavy_count = stats[0];
     R.heavy_scratch = ((uint64_t)stats[3] << 32) | stats[2];

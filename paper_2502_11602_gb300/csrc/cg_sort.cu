@@ -338,7 +338,7 @@ cudaError_t radix_sort_pairs(const uint32_t* keys, int64_t n, int key_bits, uint
   int passes = (key_bits + 7) / 8;
   if (passes > 4) passes = 4;
   if (passes == 0) {
-    cudaError_t e = cudaMemcpyAsync(keys_sorted, keys, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = dev_copy(keys_sorted, keys, (size_t)n * 4, st);
     if (e != cudaSuccess) return e;
     iota_kernel<<<grid_for(n, 256), 256, 0, st>>>(vals_sorted, n); note_launch();
     return cudaGetLastError();
