@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
     uint32_t K = len;
     for (int o = 16; o > 0; o >>= 1) K += __shfl_xor_sync(0xffffffffu, K, o);
     big |= K > (uint32_t)KW;
+    // the binary32 warp kernels compare against finite thresholds only
+    if (PREC == 1) big |= !(fmaxf(thr.s_hi, thr.c_hi) < 3.0e38f);
     const uint32_t W = big ? 0u : (K + 31u) / 32u;
     BlockPlan* P = plans + b;
     if (len > 0) {
@@ -446,10 +448,10 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
 //   3. the records are gathered run by run into their slots, in the pair
 //      layout (pair_slot), so that packed f32x2 arithmetic tests two
 //      candidates per instruction from broadcast shared-memory reads;
-//   4. lanes = (query, slice of the 32-candidate words): one 32-bit hit mask
-//      per (word, query), stored word-major ([word][query], coalesced);
-//      candidates inside the proven error band of r2 are decided in binary64
-//      on the exact coordinates.
+//   4. the (word, query) items of the group, word-major, spread evenly over
+//      the slot's lanes: one 32-bit hit mask per item, stored word-major
+//      ([word][query], coalesced); candidates inside the proven error band
+//      of r2 are decided in binary64 on the exact coordinates.
 // The fill pass reads the sorted ids and the masks back.
 template <int KC>
 struct C5 {
@@ -459,27 +461,80 @@ struct C5 {
   static constexpr size_t PH1 = 4 * (size_t)KC + 4 * (size_t)NBK + 2 * (size_t)KC;  // ids, buckets, order
   static constexpr size_t R1 = ((PH2 > PH1 ? PH2 : PH1) + 15) / 16 * 16;
   static constexpr size_t SLOT = 2 * (size_t)KC;                                    // id-order slot of each candidate
-  static constexpr size_t RUNS = 4 * (2 * 36 + 4 + 2 * 4);
-  // a slot of gw warps: the group's tables plus 32 query counters per warp
-  __host__ __device__ static constexpr size_t per_slot(int gw) { return (R1 + SLOT + RUNS + 4 * 32 * (size_t)gw + 15) / 16 * 16; }
+  static constexpr size_t RUNS = 4 * (2 * 36 + 4 + 2 * 8);                          // runs, sbox, wred (GW <= 8)
+  // 16-bit hit counter per query, two per word: in the slot table, which
+  // the tests no longer need
+  static_assert(2 * (size_t)QB2 <= SLOT, "query counters overlay the slot table");
+  // a slot of gw warps: the group's tables
+  __host__ __device__ static constexpr size_t per_slot(int) { return (R1 + SLOT + RUNS + 15) / 16 * 16; }
 };
 
+// The binary32 values of a candidate pair (packed): squared distance for the
+// sphere, its xy part for the cylinder, largest squared axis offset for the
+// cube.
+template <int KERN>
+__device__ __forceinline__ unsigned long long pair_vals(const ulonglong2& xy, unsigned long long zz,
+                                                        unsigned long long QX, unsigned long long QY,
+                                                        unsigned long long QZ) {
+  const unsigned long long DX = sub2(xy.x, QX), DY = sub2(xy.y, QY);
+  if (KERN == CG_CYLINDER) return fma2(DY, DY, mul2(DX, DX));
+  const unsigned long long DZ = sub2(zz, QZ);
+  if (KERN == CG_SPHERE) return fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
+  float a0, a1, b0, b1, c0, c1;
+  upk(mul2(DX, DX), a0, a1);
+  upk(mul2(DY, DY), b0, b1);
+  upk(mul2(DZ, DZ), c0, c1);
+  return pk(fmaxf(fmaxf(a0, b0), c0), fmaxf(fmaxf(a1, b1), c1));
+}
 template <int KERN>
 __device__ __forceinline__ void pair_test(const ulonglong2& xy, unsigned long long zz, unsigned long long QX,
                                           unsigned long long QY, unsigned long long QZ, float& v0, float& v1) {
-  const unsigned long long DX = sub2(xy.x, QX), DY = sub2(xy.y, QY), DZ = sub2(zz, QZ);
-  if (KERN == CG_SPHERE) {
-    upk(fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX))), v0, v1);
-  } else if (KERN == CG_CYLINDER) {
-    upk(fma2(DY, DY, mul2(DX, DX)), v0, v1);
-  } else {
-    float a0, a1, b0, b1, c0, c1;
-    upk(mul2(DX, DX), a0, a1);
-    upk(mul2(DY, DY), b0, b1);
-    upk(mul2(DZ, DZ), c0, c1);
-    v0 = fmaxf(fmaxf(a0, b0), c0);
-    v1 = fmaxf(fmaxf(a1, b1), c1);
+  upk(pair_vals<KERN>(xy, zz, QX, QY, QZ), v0, v1);
+}
+
+// m << 1 with the sign bit of x shifted in (one funnel shift).
+__device__ __forceinline__ uint32_t push_sign(uint32_t m, float x) {
+  uint32_t d;
+  asm("shf.l.wrap.b32 %0, %1, %2, 1;" : "=r"(d) : "r"(__float_as_uint(x)), "r"(m));
+  return d;
+}
+
+// Hit masks of one 32-candidate word against one query: bit j of *in is set
+// when the binary32 value of candidate j is <= lo, bit j of *hi when it is
+// <= hi.  TL = pk(T_lo, T_lo) with T_lo the next binary32 above lo (0 when
+// lo < 0), TH likewise for hi (hi finite): v <= lo exactly when
+// fl(v - T_lo) < 0, since a rounded difference keeps the sign of the exact
+// one and is +0 when v == T_lo; values are >= +0 or +inf (padding, never
+// below a finite T).
+template <int KERN>
+__device__ __forceinline__ void word_masks(const ulonglong2* __restrict__ xyw, const unsigned long long* __restrict__ zw,
+                                           unsigned long long QX, unsigned long long QY, unsigned long long QZ,
+                                           unsigned long long TL, unsigned long long TH, uint32_t& in,
+                                           uint32_t& hi) {
+  // four independent chains of 8 candidates (bytes 3..0), candidate 8c+7
+  // first in chain c, so that it ends in bit 8c+7
+  uint32_t mi[4] = {0, 0, 0, 0}, mh[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 3; k >= 0; --k) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int pr = 4 * c + k;
+      const unsigned long long V = pair_vals<KERN>(xyw[pr], zw[pr], QX, QY, QZ);
+      float l0, l1, h0, h1;
+      upk(sub2(V, TL), l0, l1);
+      upk(sub2(V, TH), h0, h1);
+      mi[c] = push_sign(push_sign(mi[c], l1), l0);
+      mh[c] = push_sign(push_sign(mh[c], h1), h0);
+    }
   }
+  in = (mi[3] << 24) | (mi[2] << 16) | (mi[1] << 8) | mi[0];
+  hi = (mh[3] << 24) | (mh[2] << 16) | (mh[1] << 8) | mh[0];
+}
+
+// The comparison constants of word_masks for a threshold t (t < FLT_MAX).
+__device__ __forceinline__ unsigned long long above(float t) {
+  const float T = t < 0.f ? 0.f : __uint_as_float(__float_as_uint(t) + 1u);
+  return pk(T, T);
 }
 
 // GW warps share a group (a slot of the CTA): they stage and sort its
@@ -520,7 +575,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   uint32_t* roff = rstart + 36;
   uint32_t* sbox = roff + 36;                  // [4]: group, crowded flag, id range
   uint32_t* wred = sbox + 4;                   // [2 GW]: per-warp id minima / maxima
-  uint32_t* qcnt = wred + 2 * 4 + 32 * wis;    // [32] per warp: hits of its current 32 queries
+  static_assert(GW <= 8 && NWARP % GW == 0, "slot shape");
+  uint32_t* qcnt = reinterpret_cast<uint32_t*>(slot_of);  // phase 4: [QB2 / 2] hits per query, 16 bits each
   const Thresholds thr = *thr_p;
   const float4* __restrict__ pts = ix.pts32;
   const uint32_t* __restrict__ sid = ix.sid;
@@ -528,8 +584,9 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
   const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
   // the cylinder's two-term value has a smaller error than the sphere's
   // three-term one: the sphere's band bounds it
-  const float slo = KERN == CG_CUBE ? thr.c_lo : thr.s_lo;
-  const float shi = KERN == CG_CUBE ? thr.c_hi : thr.s_hi;
+  // (the plan sends every group to the general kernel when hi is not finite)
+  const unsigned long long TL = above(KERN == CG_CUBE ? thr.c_lo : thr.s_lo);
+  const unsigned long long TH = above(KERN == CG_CUBE ? thr.c_hi : thr.s_hi);
   const float far = __int_as_float(0x7f000000);  // padding candidate: its square overflows to +inf
   for (;;) {
     if (tis == 0) sbox[0] = atomicAdd(work, 1u);
@@ -681,57 +738,35 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       z[h] = far;
     }
     slot_sync<GW>(slot);
-    // 4. tests: each warp its own chunks of 32 queries; lanes = (query, slice of words)
-    for (uint32_t qg0 = 32u * wis; qg0 < nq; qg0 += 32u * GW) {
-      const uint32_t nqg = min(32u, nq - qg0);
-      const uint32_t Sl = min(Wp, 32u / nqg);
-      const uint32_t qi = lane / Sl, s = lane - qi * Sl;
-      const bool active = qi < nqg;
-      uint32_t cnt = 0, qid = 0;
-      qcnt[lane] = 0u;
-      __syncwarp();
-      if (active) {
-        const uint32_t q = qg0 + qi;
-        const float4 qq = qsrc[q0 + q];
-        qid = __float_as_uint(qq.w);
-        const unsigned long long QX = pk(qq.x, qq.x), QY = pk(qq.y, qq.y), QZ = pk(qq.z, qq.z);
-        for (uint32_t w = s; w < Wp; w += Sl) {
-          const ulonglong2* xyw = PL.xy + w * 17u;
-          const unsigned long long* zw = PL.z + w * 17u;
-          uint32_t m_in = 0;
-          float mo = INFINITY;  // smallest value above s_lo: the band test
-#pragma unroll
-          for (int pr = 0; pr < 16; ++pr) {
-            float v0, v1;
-            pair_test<KERN>(xyw[pr], zw[pr], QX, QY, QZ, v0, v1);
-            const bool i0 = v0 <= slo, i1 = v1 <= slo;
-            m_in |= (i0 ? 1u : 0u) << (2 * pr);
-            m_in |= (i1 ? 2u : 0u) << (2 * pr);
-            mo = fminf(mo, fminf(i0 ? INFINITY : v0, i1 ? INFINITY : v1));
-          }
-          if (mo <= shi) {  // rare: decide the band in binary64
-            for (int pr = 0; pr < 16; ++pr) {
-              float v[2];
-              pair_test<KERN>(xyw[pr], zw[pr], QX, QY, QZ, v[0], v[1]);
-              for (int h = 0; h < 2; ++h) {
-                const uint32_t j = w * 32u + 2u * pr + h;
-                if (v[h] > slo && v[h] <= shi && j < K) {
-                  const uint32_t cid = __ldcg(ids + io + j);
-                  if (exact_in<KERN>(ix.xyz64 + 3 * (size_t)cid, q64 + 3 * (size_t)qid, thr.r2))
-                    m_in |= 1u << (2 * pr + h);
-                }
-              }
-            }
-          }
-          mb[w * nq + q] = m_in;
-          cnt += __popc(m_in);
-        }
+    // 4. tests: items (word w, query q) in word-major order, spread evenly
+    // over the slot's lanes; consecutive lanes take consecutive queries of
+    // one word, so that candidate reads are broadcasts and the mask stores
+    // coalesce
+    for (uint32_t t = tis; t < (nq + 1u) / 2u; t += ST) qcnt[t] = 0u;
+    slot_sync<GW>(slot);
+    const uint32_t items = Wp * nq;
+    const float inv_nq = 1.0f / (float)nq;
+    for (uint32_t it = tis; it < items; it += ST) {
+      uint32_t w = (uint32_t)((float)it * inv_nq);  // exact after one correction (items < 2^16)
+      if (w * nq > it) --w;
+      else if ((w + 1u) * nq <= it) ++w;
+      const uint32_t q = it - w * nq;
+      const float4 qq = qsrc[q0 + q];
+      const unsigned long long QX = pk(qq.x, qq.x), QY = pk(qq.y, qq.y), QZ = pk(qq.z, qq.z);
+      uint32_t m_in, m_hi;
+      word_masks<KERN>(PL.xy + w * 17u, PL.z + w * 17u, QX, QY, QZ, TL, TH, m_in, m_hi);
+      for (uint32_t band = m_hi & ~m_in; band != 0u; band &= band - 1u) {  // rare: decide in binary64
+        const uint32_t j = w * 32u + (uint32_t)(__ffs(band) - 1);
+        const uint32_t cid = __ldcg(ids + io + j);
+        if (exact_in<KERN>(ix.xyz64 + 3 * (size_t)cid, q64 + 3 * (size_t)__float_as_uint(qq.w), thr.r2))
+          m_in |= band & (0u - band);
       }
-      if (active) atomicAdd(&qcnt[qi], cnt);
-      __syncwarp();
-      if (active && s == 0) counts[qid] = qcnt[qi];
-      __syncwarp();
+      mb[w * nq + q] = m_in;
+      atomicAdd(&qcnt[q >> 1], (uint32_t)__popc(m_in) << (16u * (q & 1u)));
     }
+    slot_sync<GW>(slot);
+    for (uint32_t t = tis; t < nq; t += ST)
+      counts[__float_as_uint(qsrc[q0 + t].w)] = (qcnt[t >> 1] >> (16u * (t & 1u))) & 0xffffu;
     slot_sync<GW>(slot);  // the next group overwrites the slot's tables
   }
 }
@@ -1018,32 +1053,35 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
                                   const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
                                   uint32_t* status, const cudaStream_t* sts) {
-  // size classes: K <= 512 (a warp per group), <= 1024 (two warps per
-  // group), <= 2048 (four); 4 warps per CTA; work[0..2] are their group
+  // size classes: K <= 512 (a warp per group, 8 warps per CTA), <= 1024
+  // (two warps per group, 16 per CTA), <= 2048 (four, 4 per CTA): shapes
+  // measured fastest on the 12M ALS tile; work[0..2] are their group
   // counters, sts[0..2] their streams
 #define CG_C5(KN, KC, NW, GW, CLS, WORK)                                                         \
   do {                                                                                            \
     auto kfn = radius_count5_kernel<KN, KC, NW, GW>;                                             \
     const size_t smem = C5<KC>::per_slot(GW) * (NW / GW);                                        \
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    cudaError_t le = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (le != cudaSuccess) return le;                                                             \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
     cudaStream_t st = sts[CLS];                                                                  \
     ProfScope prof(CLS == 2 ? "radius_count5_2k" : (CLS ? "radius_count5_1k" : "radius_count5_512"), st); \
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, ids, WORK, status, \
                                   CLS);                                                           \
     note_launch();                                                                                \
+    if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
   if (kern == CG_SPHERE) {
-    CG_C5(CG_SPHERE, 512, 4, 1, 0u, work);
-    CG_C5(CG_SPHERE, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_SPHERE, 512, 8, 1, 0u, work);
+    CG_C5(CG_SPHERE, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_SPHERE, 2048, 4, 4, 2u, work + 2);
   } else if (kern == CG_CYLINDER) {
-    CG_C5(CG_CYLINDER, 512, 4, 1, 0u, work);
-    CG_C5(CG_CYLINDER, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_CYLINDER, 512, 8, 1, 0u, work);
+    CG_C5(CG_CYLINDER, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_CYLINDER, 2048, 4, 4, 2u, work + 2);
   } else {
-    CG_C5(CG_CUBE, 512, 4, 1, 0u, work);
-    CG_C5(CG_CUBE, 1024, 4, 2, 1u, work + 1);
+    CG_C5(CG_CUBE, 512, 8, 1, 0u, work);
+    CG_C5(CG_CUBE, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_CUBE, 2048, 4, 4, 2u, work + 2);
   }
 #undef CG_C5
@@ -1058,16 +1096,20 @@ cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const 
   do {                                                                                            \
     auto kfn = radius_fill5_kernel<KC, NW, GW>;                                                  \
     const size_t smem = F5<KC>::per_slot(GW) * (NW / GW);                                        \
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);           \
+    cudaError_t le = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (le != cudaSuccess) return le;                                                             \
     const int g = resident_grid(kfn, NW * 32, smem);                                             \
     cudaStream_t st = sts[CLS];                                                                  \
     ProfScope prof(CLS == 2 ? "radius_fill5_2k" : (CLS ? "radius_fill5_1k" : "radius_fill5_512"), st); \
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, plans, moff, idoff, masks, ids, offsets, out, WORK, status, CLS); \
     note_launch();                                                                                \
+    if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
-  CG_F5(512, 4, 1, 0u, work);
-  CG_F5(1024, 4, 2, 1u, work + 1);
-  CG_F5(2048, 4, 4, 2u, work + 2);
+  // a warp per group up to 1024 candidates, two above; 8 warps per CTA
+  // (measured fastest on the 12M ALS tile)
+  CG_F5(512, 8, 1, 0u, work);
+  CG_F5(1024, 8, 1, 1u, work + 1);
+  CG_F5(2048, 8, 2, 2u, work + 2);
 #undef CG_F5
   return cudaGetLastError();
 }
