@@ -251,7 +251,7 @@ def _alg_tests(xyz, r: float, cell: float) -> int:
 # binary32 lane operations of one sphere test: 3 subtractions, 1 multiply,
 # 2 fused multiply-adds, 1 comparison
 OPS_PER_TEST = 7
-# sources of the kernels whose DRAM traffic profiles/traffic.json records
+# sources of the kernels whose DRAM traffic profiles/traffic_radius_als12m.txt records
 TRAFFIC_SRC = ["cg_radius2.cu", "cg_query.cu", "cg_query.cuh", "cg_internal.cuh"]
 COUNT_PHASES = ("radius_count5_1k", "radius_count5_2k", "radius_count2", "radius_v1_count")
 FILL_PHASES = ("radius_fill5_1k", "radius_fill5_2k", "radius_fill2", "radius_v1_fill", "radius_row_sort")
@@ -411,9 +411,9 @@ def run_ours(args):
     fill_k = per_step.get("radius_fill_kernels", sum(per_step.get(k, 0.0) for k in FILL_PHASES))
     ncell = int(math.floor((xyz[:, 0].max() - xyz[:, 0].min()) / CELL) + 1) * \
         int(math.floor((xyz[:, 1].max() - xyz[:, 1].min()) / CELL) + 1)
+    tests = _alg_tests(xyz, RADIUS, CELL)
     if count_k >= fill_k:
         # the count kernels are bound by the binary32 tests, not by memory
-        tests = _alg_tests(xyz, RADIUS, CELL)
         sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
         alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
         achieved = OPS_PER_TEST * tests / (count_k * 1e-3) / 1e12
@@ -430,6 +430,21 @@ def run_ours(args):
                 "frac": achieved / peak,
                 "traffic": _traffic("radius_fill_kernels", TRAFFIC_SRC),
                 "algorithmic_bytes": alg, "ms_per_launch": fill_k}
+
+    # the whole step against HBM, from the bytes-touched model of one build +
+    # count + fill (binary32 records): build reads the points (24 B) and
+    # writes keys, sorted keys and ids (12 B), records (16 B) and the exact
+    # copy (24 B); each query pass reads the records (16 B/pt) and the cell
+    # table; count writes counts and the offsets (4 + 8 B/query); fill reads
+    # the offsets (8 B/query) and writes 4 B per neighbour
+    model = {"build": 24 * n + 12 * n + 16 * n + 24 * n,
+             "count": 16 * n + 4 * (ncell + 1) + 12 * n,
+             "fill": 16 * n + 4 * (ncell + 1) + 8 * n + 4 * total}
+    model_bytes = sum(model.values())
+    hbm_model = {"bytes_per_step": model_bytes, "terms": model,
+                 "achieved_gbs": model_bytes / (ms * 1e-3) / 1e9, "peak_gbs": peak, "peak_kind": peak_kind,
+                 "frac": model_bytes / (ms * 1e-3) / 1e9 / peak,
+                 "alu_floor_ms": OPS_PER_TEST * tests / (152 * 128 * 2070e6) * 1e3}
 
     # secondary measurements on the same tile: k-NN (k = 16) and the binary64 path
     h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, prec)
@@ -474,7 +489,7 @@ def run_ours(args):
         "e2e": {"value": n_all / (_max_over_ranks(e2e_ms, dist, dev) * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "pipelined_steps": e2e_steps, "serial_ms_per_step": e2e_serial_ms,
                 "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": (n + 1) * 8 + total * 4},
-        "roofline": roof, "clocks": clk, "gpu_launches": launches,
+        "roofline": roof, "hbm_model": hbm_model, "clocks": clk, "gpu_launches": launches,
         "knn16": {"queries_per_s": n_all / (_max_over_ranks(statistics.mean(kt), dist, dev) * 1e-3),
                   "ms": statistics.mean(kt)},
     }

@@ -776,13 +776,16 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
 // queries: their masks (word-major, one coalesced row per word) to shared
 // memory; rows are expanded in lane segments of seg = 2^ceil(log2 Wp) lanes,
 // 32 / seg rows at a time (one word per lane): a segmented scan of the
-// words' popcounts places each word's hits, whose ids (ascending) go
-// straight to their place in the row.  Groups of more than 32 words use the
-// whole warp per row, words 32..63 placed after all of words 0..31.
+// words' popcounts places each word's hits (ids ascending) in the row.  The
+// row is assembled in the segment's share of a per-warp staging buffer and
+// then written out by consecutive lanes (coalesced); a row longer than its
+// share is written hit by hit instead.  Groups of more than 32 words use
+// the whole warp per row, words 32..63 placed after all of words 0..31.
 template <int KC>
 struct F5 {
   static constexpr int WMAX = KC / 32;
-  __host__ __device__ static constexpr size_t per_warp() { return 4 * (size_t)WMAX * 33 + 8 * 32; }
+  static constexpr int RB = 512;  // staging entries per warp
+  __host__ __device__ static constexpr size_t per_warp() { return 4 * (size_t)WMAX * 33 + 8 * 32 + 4 * (size_t)RB; }
   __host__ __device__ static constexpr size_t per_slot(int gw) {
     return (4 * (size_t)KC + per_warp() * (size_t)gw + 15) / 16 * 16;
   }
@@ -811,6 +814,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
   unsigned char* wbase = base + 4 * (size_t)KC + (size_t)wis * L::per_warp();
   uint32_t* ms = reinterpret_cast<uint32_t*>(wbase);                                   // [WMAX][33]
   long long* soff = reinterpret_cast<long long*>(ms + L::WMAX * 33);                  // [32]
+  int32_t* rbuf = reinterpret_cast<int32_t*>(soff + 32);                               // [RB]
   const float4* __restrict__ qsrc = qs.all_points ? ix.pts32 : qs.qrec;
   for (;;) {
     if (tis == 0) s_grp[slot] = atomicAdd(work, 1u);
@@ -840,6 +844,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
       if (L::WMAX <= 32 || Wp <= 32) {
         // each word's hits go straight to their place in the row
         const uint32_t rows = 32u / seg, j = lane / seg, wl = lane % seg;
+        const uint32_t share = (uint32_t)L::RB / rows;  // staging entries of this segment
+        int32_t* rb = rbuf + j * share;
         for (uint32_t t0 = 0; t0 < nc; t0 += rows) {
           const uint32_t t = t0 + j;
           const bool live = t < nc;
@@ -850,36 +856,55 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o, seg);
             if (wl >= o) incl += y;
           }
-          int32_t* dst = out + (live ? soff[t] : 0) + (incl - c);
+          const uint32_t H = __shfl_sync(0xffffffffu, incl, seg - 1, seg);  // hits of the row
+          const bool staged = H <= share;
+          int32_t* dst = (staged ? rb : out + (live ? soff[t] : 0)) + (incl - c);
           while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
             *dst++ = (int32_t)sids[wl * 32 + bit];
           }
+          __syncwarp();
+          if (staged && live) {
+            int32_t* row = out + soff[t];
+            for (uint32_t u = wl; u < H; u += seg) row[u] = rb[u];
+          }
+          __syncwarp();  // the next rows reuse the staging buffer
         }
       } else {
         for (uint32_t t = 0; t < nc; ++t) {
           // words 0..31 (lane = word), then words 32..63 after all of them
-          int32_t* row = out + soff[t];
-          uint32_t tot = 0;
+          uint32_t m[2], c[2], incl[2];
 #pragma unroll
           for (int half = 0; half < 2; ++half) {
             const uint32_t w = lane + 32u * half;
-            uint32_t m = w < Wp ? ms[w * 33 + t] : 0u;
-            const uint32_t c = __popc(m);
-            uint32_t incl = c;
+            m[half] = w < Wp ? ms[w * 33 + t] : 0u;
+            c[half] = __popc(m[half]);
+            incl[half] = c[half];
             for (int o = 1; o < 32; o <<= 1) {
-              const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-              if (lane >= (unsigned)o) incl += y;
-            }
-            int32_t* dst = row + tot + (incl - c);
-            tot += __shfl_sync(0xffffffffu, incl, 31);
-            while (m) {
-              const int bit = __ffs(m) - 1;
-              m &= m - 1;
-              *dst++ = (int32_t)sids[w * 32 + bit];
+              const uint32_t y = __shfl_up_sync(0xffffffffu, incl[half], o);
+              if (lane >= (unsigned)o) incl[half] += y;
             }
           }
+          const uint32_t T0 = __shfl_sync(0xffffffffu, incl[0], 31);
+          const uint32_t H = T0 + __shfl_sync(0xffffffffu, incl[1], 31);
+          const bool staged = H <= (uint32_t)L::RB;
+          int32_t* row = out + soff[t];
+          int32_t* base = staged ? rbuf : row;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            int32_t* dst = base + (half ? T0 : 0u) + (incl[half] - c[half]);
+            uint32_t mm = m[half];
+            while (mm) {
+              const int bit = __ffs(mm) - 1;
+              mm &= mm - 1;
+              *dst++ = (int32_t)sids[(lane + 32u * half) * 32 + bit];
+            }
+          }
+          __syncwarp();
+          if (staged)
+            for (uint32_t u = lane; u < H; u += 32) row[u] = rbuf[u];
+          __syncwarp();  // the next row reuses the staging buffer
         }
       }
     }
@@ -1105,11 +1130,11 @@ cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const 
     note_launch();                                                                                \
     if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
-  // a warp per group up to 1024 candidates, two above; 8 warps per CTA
-  // (measured fastest on the 12M ALS tile)
-  CG_F5(512, 8, 1, 0u, work);
+  // a warp per group up to 1024 candidates, two above; 16 / 8 / 4 warps
+  // per CTA (measured fastest on the 12M ALS tile)
+  CG_F5(512, 16, 1, 0u, work);
   CG_F5(1024, 8, 1, 1u, work + 1);
-  CG_F5(2048, 8, 2, 2u, work + 2);
+  CG_F5(2048, 4, 2, 2u, work + 2);
 #undef CG_F5
   return cudaGetLastError();
 }
