@@ -55,51 +55,21 @@ __global__ void bbox_init_kernel(unsigned long long* bb, int ntiles) {
 
 constexpr int kBoxItems = 8;
 
-__global__ void __launch_bounds__(kThreads) bbox_kernel(const double* __restrict__ xyz, int64_t n,
-                                                        const int64_t* __restrict__ toff,
-                                                        int ntiles, unsigned long long* bb,
-                                                        uint32_t* status) {
-  __shared__ double s_red[6][kThreads / 32];
-  __shared__ int s_t0, s_t1;
-  const int64_t base = (int64_t)blockIdx.x * kThreads * kBoxItems;
-  if (base >= n) return;
-  int64_t last = base + kThreads * kBoxItems - 1;
-  if (last >= n) last = n - 1;
-  if (threadIdx.x == 0) {
-    // tiles of the first and last point of this block
-    int a = 0, b = ntiles - 1;
-    while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= base) a = m; else b = m - 1; }
-    s_t0 = a;
-    a = 0; b = ntiles - 1;
-    while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= last) a = m; else b = m - 1; }
-    s_t1 = a;
-  }
-  __syncthreads();
-  const bool uniform = s_t0 == s_t1;
-  double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  bool bad = false;
-  for (int j = 0; j < kBoxItems; ++j) {
-    int64_t p = base + (int64_t)j * kThreads + threadIdx.x;
-    if (p >= n) break;
-    double v[3] = {xyz[3 * p], xyz[3 * p + 1], xyz[3 * p + 2]};
-    bad |= !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]));
-    if (uniform) {
-      for (int a = 0; a < 3; ++a) { mn[a] = fmin(mn[a], v[a]); mx[a] = fmax(mx[a], v[a]); }
-    } else {
-      int a = s_t0, b = s_t1;
-      while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= p) a = m; else b = m - 1; }
-      for (int ax = 0; ax < 3; ++ax) {
-        atomicMin(bb + 6 * a + ax, dbl_to_ord(v[ax]));
-        atomicMax(bb + 6 * a + 3 + ax, dbl_to_ord(v[ax]));
-      }
-    }
-  }
-  if (bad) atomicOr(status, ST_NONFINITE);
-  if (!uniform) return;
+// Coordinates are reduced as their order-preserving 64-bit images
+// (dbl_to_ord): integer minima and maxima run on the ALU pipe, binary64
+// ones would run on the narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long ord_bits(unsigned long long u) {
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ bool finite_bits(unsigned long long u) { return ((u >> 52) & 0x7ffull) != 0x7ffull; }
+
+// Block-wide min / max of the running box, merged into tile t's entry.
+__device__ __forceinline__ void bbox_flush(unsigned long long (&mn)[3], unsigned long long (&mx)[3], int t,
+                                           unsigned long long* bb, unsigned long long (*s_red)[kThreads / 32]) {
   for (int a = 0; a < 3; ++a) {
     for (int o = 16; o > 0; o >>= 1) {
-      mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-      mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+      mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+      mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
     }
   }
   const int w = threadIdx.x >> 5;
@@ -107,12 +77,92 @@ __global__ void __launch_bounds__(kThreads) bbox_kernel(const double* __restrict
     for (int a = 0; a < 3; ++a) { s_red[a][w] = mn[a]; s_red[3 + a][w] = mx[a]; }
   __syncthreads();
   if (threadIdx.x < 6) {
-    int a = threadIdx.x;
-    double r = s_red[a][0];
-    for (int k = 1; k < kThreads / 32; ++k) r = a < 3 ? fmin(r, s_red[a][k]) : fmax(r, s_red[a][k]);
-    if (a < 3) atomicMin(bb + 6 * s_t0 + a, dbl_to_ord(r));
-    else atomicMax(bb + 6 * s_t0 + a, dbl_to_ord(r));
+    const int a = threadIdx.x;
+    unsigned long long r = s_red[a][0];
+    for (int k = 1; k < kThreads / 32; ++k) r = a < 3 ? min(r, s_red[a][k]) : max(r, s_red[a][k]);
+    if (a < 3) atomicMin(bb + 6 * t + a, r);
+    else atomicMax(bb + 6 * t + a, r);
   }
+  __syncthreads();
+  for (int a = 0; a < 3; ++a) { mn[a] = ~0ull; mx[a] = 0ull; }
+}
+
+// Persistent grid over chunks of kThreads * kBoxItems points: a block keeps
+// one running box while its chunks stay in one tile and merges it into the
+// tile's entry when the tile changes and at the end; a chunk that straddles
+// tiles merges point by point.
+__global__ void __launch_bounds__(kThreads) bbox_kernel(const double* __restrict__ xyz, int64_t n,
+                                                        const int64_t* __restrict__ toff,
+                                                        int ntiles, unsigned long long* bb,
+                                                        uint32_t* status) {
+  __shared__ unsigned long long s_red[6][kThreads / 32];
+  __shared__ int s_t0, s_t1;
+  constexpr int64_t kChunk = (int64_t)kThreads * kBoxItems;
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  const unsigned long long* __restrict__ xb = reinterpret_cast<const unsigned long long*>(xyz);
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  int cur = -1;  // tile of the running box (block-uniform)
+  bool bad = false;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int64_t base = c * kChunk;
+    const int64_t last = min(base + kChunk, n) - 1;
+    if (threadIdx.x == 0) {
+      // tiles of the first and last point of this chunk
+      int a = 0, b = ntiles - 1;
+      while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= base) a = m; else b = m - 1; }
+      s_t0 = a;
+      a = 0; b = ntiles - 1;
+      while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= last) a = m; else b = m - 1; }
+      s_t1 = a;
+    }
+    __syncthreads();
+    const int t0 = s_t0, t1 = s_t1;
+    __syncthreads();  // s_t0 / s_t1 are rewritten for the next chunk
+    const bool uniform = t0 == t1;
+    if (uniform && t0 != cur) {
+      if (cur >= 0) bbox_flush(mn, mx, cur, bb, s_red);
+      cur = t0;
+    }
+    // every load of the thread first (all in flight), then the reductions
+    unsigned long long v[kBoxItems][3];
+#pragma unroll
+    for (int j = 0; j < kBoxItems; ++j) {
+      const int64_t p = base + (int64_t)j * kThreads + threadIdx.x;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[j][a] = p < n ? __ldg(xb + 3 * p + a) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kBoxItems; ++j) {
+      const int64_t p = base + (int64_t)j * kThreads + threadIdx.x;
+      if (p >= n) break;
+      bad |= !(finite_bits(v[j][0]) && finite_bits(v[j][1]) && finite_bits(v[j][2]));
+      if (uniform) {
+        for (int a = 0; a < 3; ++a) {
+          const unsigned long long o = ord_bits(v[j][a]);
+          mn[a] = min(mn[a], o);
+          mx[a] = max(mx[a], o);
+        }
+      } else {
+        int a = t0, b = t1;
+        while (a < b) { int m = (a + b + 1) >> 1; if (toff[m] <= p) a = m; else b = m - 1; }
+        for (int ax = 0; ax < 3; ++ax) {
+          atomicMin(bb + 6 * a + ax, ord_bits(v[j][ax]));
+          atomicMax(bb + 6 * a + 3 + ax, ord_bits(v[j][ax]));
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+  if (cur >= 0) bbox_flush(mn, mx, cur, bb, s_red);
+}
+
+// Grid of bbox_kernel: a few resident blocks per SM.
+unsigned bbox_grid(int64_t n) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int64_t chunks = (n + (int64_t)kThreads * kBoxItems - 1) / ((int64_t)kThreads * kBoxItems);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(chunks, 4 * (int64_t)sms));
 }
 
 // --- B1: keys --------------------------------------------------------------
@@ -352,8 +402,7 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   bbox_init_kernel<<<(6 * ntiles + 255) / 256, 256, 0, st>>>(bb, ntiles); note_launch();
   {
     ProfScope prof("build_bbox", st);
-    int64_t blocks = (n + kThreads * kBoxItems - 1) / (kThreads * kBoxItems);
-    bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, toff_dev, ntiles, bb, ix->status); note_launch();
+    bbox_kernel<<<bbox_grid(n), kThreads, 0, st>>>(xyz, n, toff_dev, ntiles, bb, ix->status); note_launch();
   }
   CG_CUDA(cudaGetLastError());
   std::vector<unsigned long long> bbh(6 * ntiles);
@@ -582,8 +631,7 @@ cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream
   cudaError_t e;
   bbox_init_kernel<<<(6 * T + 255) / 256, 256, 0, st>>>(w.bb, T); note_launch();
   {
-    int64_t blocks = (n + kThreads * kBoxItems - 1) / (kThreads * kBoxItems);
-    bbox_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(xyz, n, w.toff, T, w.bb, ix->status); note_launch();
+    bbox_kernel<<<bbox_grid(n), kThreads, 0, st>>>(xyz, n, w.toff, T, w.bb, ix->status); note_launch();
   }
   tiles_refresh_kernel<<<(T + 127) / 128, 128, 0, st>>>(ix->tiles, T, w.bb, ix->dim, ix->status); note_launch();
   key_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(xyz, n, ix->tiles, T, ix->dim, w.keys); note_launch();

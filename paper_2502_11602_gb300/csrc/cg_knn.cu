@@ -385,16 +385,19 @@ __device__ __forceinline__ float centre_dist(const float4& r, float cx, float cy
 
 template <int L>
 __device__ __forceinline__ void topl_insert(float (&v)[L], uint32_t (&id)[L], float d, uint32_t j) {
+  // v ascending: d goes before the first entry it is below (after equal
+  // ones); every position is computed from the old list, so the selects do
+  // not form one dependent chain
+  bool c[L];
 #pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const bool p = d < v[i];
-    const float tv = v[i];
-    const uint32_t ti = id[i];
-    v[i] = p ? d : tv;
-    id[i] = p ? j : ti;
-    d = p ? tv : d;
-    j = p ? ti : j;
+  for (int i = 0; i < L; ++i) c[i] = d < v[i];
+#pragma unroll
+  for (int i = L - 1; i > 0; --i) {
+    v[i] = c[i - 1] ? v[i - 1] : (c[i] ? d : v[i]);
+    id[i] = c[i - 1] ? id[i - 1] : (c[i] ? j : id[i]);
   }
+  v[0] = c[0] ? d : v[0];
+  id[0] = c[0] ? j : id[0];
 }
 
 template <int KC, int L, int NWARP>

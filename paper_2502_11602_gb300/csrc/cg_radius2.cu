@@ -1078,7 +1078,7 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
                                   const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
                                   uint32_t* status, const cudaStream_t* sts) {
-  // size classes: K <= 512 (a warp per group, 8 warps per CTA), <= 1024
+  // size classes: K <= 512 (a warp per group, 7 warps per CTA), <= 1024
   // (two warps per group, 16 per CTA), <= 2048 (four, 4 per CTA): shapes
   // measured fastest on the 12M ALS tile; work[0..2] are their group
   // counters, sts[0..2] their streams
@@ -1097,15 +1097,15 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
     if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
   if (kern == CG_SPHERE) {
-    CG_C5(CG_SPHERE, 512, 8, 1, 0u, work);
+    CG_C5(CG_SPHERE, 512, 7, 1, 0u, work);
     CG_C5(CG_SPHERE, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_SPHERE, 2048, 4, 4, 2u, work + 2);
   } else if (kern == CG_CYLINDER) {
-    CG_C5(CG_CYLINDER, 512, 8, 1, 0u, work);
+    CG_C5(CG_CYLINDER, 512, 7, 1, 0u, work);
     CG_C5(CG_CYLINDER, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_CYLINDER, 2048, 4, 4, 2u, work + 2);
   } else {
-    CG_C5(CG_CUBE, 512, 8, 1, 0u, work);
+    CG_C5(CG_CUBE, 512, 7, 1, 0u, work);
     CG_C5(CG_CUBE, 1024, 16, 2, 1u, work + 1);
     CG_C5(CG_CUBE, 2048, 4, 4, 2u, work + 2);
   }
