@@ -351,12 +351,21 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
 constexpr int K5_NB = 64;
 constexpr int K5_Q = 8;  // queued candidates per lane
 
+// Shared memory of a slot of gw warps: the group's staged box (records,
+// buckets, spans, a few broadcast words), then one candidate queue per warp.
 template <int KC>
 struct K5Smem {
-  static constexpr size_t per_warp = 16 * (size_t)KC + (size_t)KC + 4 * (2 * K5_NB + 2) + 4 * 2 * 12 +
-                                     8 * (size_t)K5_Q * 32;
-  static constexpr size_t per_warp_aligned = (per_warp + 15) / 16 * 16;
+  static constexpr size_t tables = (16 * (size_t)KC + (size_t)KC + 4 * (2 * K5_NB + 2) + 4 * 2 * 12 + 4 * 4 + 15) / 16 * 16;
+  static constexpr size_t queue = 8 * (size_t)K5_Q * 32;
+  __host__ __device__ static constexpr size_t per_slot(int gw) { return tables + queue * (size_t)gw; }
 };
+
+// Barrier of the GW warps of one slot (named barrier 1 + slot).
+template <int GW>
+__device__ __forceinline__ void k5_slot_sync(int slot) {
+  if (GW == 1) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(GW * 32) : "memory");
+}
 
 // wall2_lower for one box given by scalars (no array whose address is taken)
 __device__ __forceinline__ float wall2_box(const float4& q, const Tile& T, int dim, int lo0, int lo1, int lo2, int hi0,
@@ -400,7 +409,7 @@ __device__ __forceinline__ void topl_insert(float (&v)[L], uint32_t (&id)[L], fl
   id[0] = c[0] ? j : id[0];
 }
 
-template <int KC, int L, int NWARP>
+template <int KC, int L, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet qs, const Thresholds* __restrict__ thr_p,
                                                           int k, int32_t* __restrict__ out_idx,
                                                           double* __restrict__ out_d2, uint32_t* __restrict__ slow_list,
@@ -410,17 +419,22 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
   if (replan_pending(status)) return;  // the later kernels then find empty lists
   constexpr int RB = 1;
   using S = K5Smem<KC>;
+  static_assert(NWARP % GW == 0 && NWARP / GW <= 15, "slot shape");
+  constexpr int ST = GW * 32;  // threads per slot
   extern __shared__ __align__(32) unsigned char smem[];
-  unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * S::per_warp_aligned;
+  const int warp = (int)(threadIdx.x >> 5), slot = warp / GW, wis = warp % GW;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t tis = (uint32_t)wis * 32u + lane;  // thread in slot
+  unsigned char* base = smem + (size_t)slot * S::per_slot(GW);
   float4* recs = reinterpret_cast<float4*>(base);                 // [KC] in bucket order
   uint8_t* bkt = reinterpret_cast<uint8_t*>(recs + KC);           // [KC] bucket of each span-order candidate
   uint32_t* bstart = reinterpret_cast<uint32_t*>(bkt + KC);       // [NB + 1]
   uint32_t* cursor = bstart + K5_NB + 1;                          // [NB + 1]
   uint32_t* sp_start = cursor + K5_NB + 1;                        // [12]
   uint32_t* sp_off = sp_start + 12;                               // [12]
-  float* qd = reinterpret_cast<float*>(sp_off + 12);              // [Q][32] queued values
-  uint32_t* qj = reinterpret_cast<uint32_t*>(qd + K5_Q * 32);     // [Q][32] queued slots
-  const unsigned lane = threadIdx.x & 31u;
+  uint32_t* sbox = sp_off + 12;                                   // [4]: group, K
+  float* qd = reinterpret_cast<float*>(base + S::tables + S::queue * (size_t)wis);  // [Q][32] queued values
+  uint32_t* qj = reinterpret_cast<uint32_t*>(qd + K5_Q * 32);                       // [Q][32] queued slots
   const Thresholds thr = *thr_p;
   const KBound kb = make_kbound<1>(thr);
   const float4* __restrict__ pts = ix.pts32;
@@ -428,9 +442,12 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
   const double* __restrict__ q64 = qs.all_points ? ix.xyz64 : qs.q64;
   const int dim = ix.dim;
   for (;;) {
-    uint32_t b = 0;
-    if (lane == 0) b = atomicAdd(work, 1u);
-    b = __shfl_sync(0xffffffffu, b, 0);
+    // the slot's next group; its box is staged by all GW warps, whose
+    // chunks of 32 queries then share it
+    if (tis == 0) sbox[0] = atomicAdd(work, 1u);
+    k5_slot_sync<GW>(slot);
+    const uint32_t b = sbox[0];
+    k5_slot_sync<GW>(slot);
     if (b >= qs_nblocks(qs)) break;
     const uint32_t qb0 = qs.blk_beg[b], qb1 = qs.blk_beg[b + 1];
     const uint32_t bkey = qs.blk_key[b];
@@ -446,7 +463,8 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
                            (dim == 2 || (lo2 == 0 && hi2 == T.n[2] - 1));
     const int ni = hi0 - lo0 + 1, nj = hi1 - lo1 + 1;
     const int nsp = dim == 2 ? ni : ni * nj;  // <= NSP
-    // spans (one contiguous run of sorted points per grid row / column)
+    // spans (one contiguous run of sorted points per grid row / column),
+    // computed by every warp of the slot
     uint32_t len = 0, st0 = 0;
     if ((int)lane < nsp) {
       uint32_t k0, k1;
@@ -473,10 +491,10 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
     // size classes: 0: K <= 512, 1: K <= 1024, 2: K <= 2048 (and the groups too large to stage)
     if (kcls == 0 ? K > 512u : (kcls == 1 ? (K <= 512u || K > 1024u) : K <= 1024u)) continue;
     if (K > (uint32_t)KC) {  // too large to stage: the ring-by-ring path
-      for (uint32_t t = qb0 + lane; t < qb1; t += 32) slow_list[atomicAdd(slow_cnt, 1u)] = __float_as_uint(qsrc[t].w);
+      for (uint32_t t = qb0 + tis; t < qb1; t += ST) slow_list[atomicAdd(slow_cnt, 1u)] = __float_as_uint(qsrc[t].w);
       continue;
     }
-    if ((int)lane < nsp) { sp_start[lane] = st0; sp_off[lane] = incl - len; }
+    if (wis == 0 && (int)lane < nsp) { sp_start[lane] = st0; sp_off[lane] = incl - len; }
     // the group voxel's centre in offset coordinates and the bucket width
     const float cx = __fsub_rn(__fmul_rn((float)c0 + 0.5f, (float)T.s[0]), T.D[0]);
     const float cy = __fsub_rn(__fmul_rn((float)c1 + 0.5f, (float)T.s[1]), T.D[1]);
@@ -485,20 +503,20 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
     const float smax = fmaxf(fmaxf((float)T.s[0], (float)T.s[1]), dim == 3 ? (float)T.s[2] : 0.f);
     const float bw = (dim == 2 ? 1.42f : 1.74f) * ((float)RB + 0.5f) * smax / (float)K5_NB;
     const float inv_bw = 1.0f / bw;
-    for (int u = (int)lane; u <= K5_NB; u += 32) bstart[u] = 0u;
-    __syncwarp();
+    for (int u = (int)tis; u <= K5_NB; u += ST) bstart[u] = 0u;
+    k5_slot_sync<GW>(slot);
     // bucket counts, then starts, then the records in bucket order
     for (int r = 0; r < nsp; ++r) {
       const uint32_t o = sp_off[r], l = (r + 1 < nsp ? sp_off[r + 1] : K) - o, s0 = sp_start[r];
-      for (uint32_t t = lane; t < l; t += 32) {
+      for (uint32_t t = tis; t < l; t += ST) {
         const float4 r4 = __ldg(pts + s0 + t);
         const int u = min(K5_NB - 1, (int)(centre_dist(r4, cx, cy, cz, zw) * inv_bw));
         bkt[o + t] = (uint8_t)u;
         atomicAdd(&bstart[u], 1u);
       }
     }
-    __syncwarp();
-    {
+    k5_slot_sync<GW>(slot);
+    if (wis == 0) {
       const uint32_t a0 = bstart[2 * lane], a1 = bstart[2 * lane + 1];
       uint32_t inc2 = a0 + a1;
       for (int o = 1; o < 32; o <<= 1) {
@@ -513,14 +531,14 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
       cursor[2 * lane + 1] = ex + a0;
       if (lane == 31) bstart[K5_NB] = K;
     }
-    __syncwarp();
+    k5_slot_sync<GW>(slot);
     for (int r = 0; r < nsp; ++r) {
       const uint32_t o = sp_off[r], l = (r + 1 < nsp ? sp_off[r + 1] : K) - o, s0 = sp_start[r];
-      for (uint32_t t = lane; t < l; t += 32) recs[atomicAdd(&cursor[bkt[o + t]], 1u)] = __ldg(pts + s0 + t);
+      for (uint32_t t = tis; t < l; t += ST) recs[atomicAdd(&cursor[bkt[o + t]], 1u)] = __ldg(pts + s0 + t);
     }
-    __syncwarp();
-    // queries, one per lane
-    for (uint32_t qc = qb0; qc < qb1; qc += 32) {
+    k5_slot_sync<GW>(slot);
+    // queries, one per lane; each warp of the slot its own chunks of 32
+    for (uint32_t qc = qb0 + 32u * (uint32_t)wis; qc < qb1; qc += 32u * GW) {
       __syncwarp();
       const bool live = qc + lane < qb1;
       const float4 q = live ? qsrc[qc + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -955,11 +973,12 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
   // the classes' groups are disjoint: their launches run concurrently
   ProfScope prof_all("knn_fast_kernels", st);  // box classes + bounded search
   Fork f(st, 3);
-#define CG_K5(KC, L, NW, CLS)                                                                                \
+#define CG_K5(KC, L, NW, GW, CLS)                                                                            \
   do {                                                                                                       \
-    auto kfn = knn5_kernel<KC, L, NW>;                                                                       \
-    const size_t smem = K5Smem<KC>::per_warp_aligned * NW;                                                   \
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+    auto kfn = knn5_kernel<KC, L, NW, GW>;                                                                   \
+    const size_t smem = K5Smem<KC>::per_slot(GW) * (NW / GW);                                                \
+    cudaError_t le = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (le != cudaSuccess) return le;                                                                        \
     int per = 0;                                                                                             \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, NW * 32, smem);                                 \
     cudaStream_t cs = f[CLS];                                                                                \
@@ -967,19 +986,22 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
     kfn<<<sms * (per > 0 ? per : 1), NW * 32, smem, cs>>>(iv, qs, thr, k, idx, d2, slow, ctrs, bslot, br2,    \
                                                           ctrs + 9, ctrs + 4 + CLS, status, CLS);              \
     note_launch();                                                                                           \
+    if ((le = cudaGetLastError()) != cudaSuccess) return le;                                                 \
   } while (0)
+  // warps per group: 1, 2, 4 for the three classes (their groups hold about
+  // 1, 2.5 and 4 chunks of 32 queries), sharing the staged box
   if (k <= 8) {
-    CG_K5(512, 12, 4, 0u);
-    CG_K5(1024, 12, 4, 1u);
-    CG_K5(2048, 12, 2, 2u);
+    CG_K5(512, 12, 4, 1, 0u);
+    CG_K5(1024, 12, 4, 2, 1u);
+    CG_K5(2048, 12, 4, 4, 2u);
   } else if (k <= 16) {
-    CG_K5(512, 20, 4, 0u);
-    CG_K5(1024, 20, 4, 1u);
-    CG_K5(2048, 20, 2, 2u);
+    CG_K5(512, 20, 4, 1, 0u);
+    CG_K5(1024, 20, 4, 2, 1u);
+    CG_K5(2048, 20, 4, 4, 2u);
   } else {
-    CG_K5(512, 36, 4, 0u);
-    CG_K5(1024, 36, 4, 1u);
-    CG_K5(2048, 36, 2, 2u);
+    CG_K5(512, 36, 4, 1, 0u);
+    CG_K5(1024, 36, 4, 2, 1u);
+    CG_K5(2048, 36, 4, 4, 2u);
   }
 #undef CG_K5
   f.join();
