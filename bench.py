@@ -412,24 +412,25 @@ def run_ours(args):
     ncell = int(math.floor((xyz[:, 0].max() - xyz[:, 0].min()) / CELL) + 1) * \
         int(math.floor((xyz[:, 1].max() - xyz[:, 1].min()) / CELL) + 1)
     tests = _alg_tests(xyz, RADIUS, CELL)
-    if count_k >= fill_k:
-        # the count kernels are bound by the binary32 tests, not by memory
-        sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
-        alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
-        achieved = OPS_PER_TEST * tests / (count_k * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "concurrent " + "+".join(k for k in COUNT_PHASES if k in per_step),
-                "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s", "frac": achieved / alu_peak,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
-                "traffic": _traffic("radius_count_kernels", TRAFFIC_SRC),
-                "algorithmic_tests": tests, "ops_per_test": OPS_PER_TEST, "ms_per_launch": count_k}
-    else:
-        alg = 16 * n + 4 * (ncell + 1) + 8 * (n + 1) + 4 * total
-        achieved = alg / (fill_k * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "concurrent " + "+".join(k for k in FILL_PHASES if k in per_step),
-                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak,
-                "traffic": _traffic("radius_fill_kernels", TRAFFIC_SRC),
-                "algorithmic_bytes": alg, "ms_per_launch": fill_k}
+    # the count kernels are bound by the binary32 tests, not by memory; the
+    # fill kernels by writing the CSR; the longer of the two is reported as
+    # the dominant kernel, the other beside it
+    sm_mhz = float(clk.get("sm_max_mhz") or 2070.0)
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # T lane-ops/s
+    achieved = OPS_PER_TEST * tests / (count_k * 1e-3) / 1e12
+    roof_count = {"bound": "alu", "kernel": "concurrent " + "+".join(k for k in COUNT_PHASES if k in per_step),
+                  "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s", "frac": achieved / alu_peak,
+                  "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+                  "traffic": _traffic("radius_count_kernels", TRAFFIC_SRC),
+                  "algorithmic_tests": tests, "ops_per_test": OPS_PER_TEST, "ms_per_launch": count_k}
+    alg = 16 * n + 4 * (ncell + 1) + 8 * (n + 1) + 4 * total
+    achieved = alg / (fill_k * 1e-3) / 1e9
+    roof_fill = {"bound": "hbm", "kernel": "concurrent " + "+".join(k for k in FILL_PHASES if k in per_step),
+                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                 "frac": achieved / peak,
+                 "traffic": _traffic("radius_fill_kernels", TRAFFIC_SRC),
+                 "algorithmic_bytes": alg, "ms_per_launch": fill_k}
+    roof, roof_other = (roof_count, roof_fill) if count_k >= fill_k else (roof_fill, roof_count)
 
     # the whole step against HBM, from the bytes-touched model of one build +
     # count + fill (binary32 records): build reads the points (24 B) and
@@ -489,7 +490,8 @@ def run_ours(args):
         "e2e": {"value": n_all / (_max_over_ranks(e2e_ms, dist, dev) * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "pipelined_steps": e2e_steps, "serial_ms_per_step": e2e_serial_ms,
                 "h2d_bytes_per_step": n * 24, "d2h_bytes_per_step": (n + 1) * 8 + total * 4},
-        "roofline": roof, "hbm_model": hbm_model, "clocks": clk, "gpu_launches": launches,
+        "roofline": roof, "roofline_other": roof_other, "hbm_model": hbm_model, "clocks": clk,
+        "gpu_launches": launches,
         "knn16": {"queries_per_s": n_all / (_max_over_ranks(statistics.mean(kt), dist, dev) * 1e-3),
                   "ms": statistics.mean(kt)},
     }
