@@ -70,12 +70,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const Tin* __restric
 
   unsigned long long v[kScanItems];
   unsigned long long run = 0;
+  // the thread's 8 inputs as two 16-byte loads where they are whole and
+  // aligned (4-byte inputs), else one by one
+  Tin xin[kScanItems];
+  if (sizeof(Tin) == 4 && base + kScanItems <= n && ((reinterpret_cast<uintptr_t>(in + base) & 15u) == 0)) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(in + base));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(in + base) + 1);
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) xin[i] = (Tin)w[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) xin[i] = (base + i < n) ? in[base + i] : (Tin)0;
+  }
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    int64_t e = base + i;
-    unsigned long long x = (e < n) ? (unsigned long long)in[e] : 0ull;
     v[i] = run;  // exclusive within the thread
-    run += x;
+    run += (unsigned long long)xin[i];
   }
   // block-wide exclusive scan of the thread totals
   unsigned long long incl = run;
@@ -107,12 +118,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const Tin* __restric
   }
   __syncthreads();
   const unsigned long long off = s_prefix + s_warp[warp] + (incl - run);
+  Tout o[kScanItems];
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    int64_t e = base + i;
-    if (e < n) out[e] = (Tout)(off + v[i]);
-    if (e == n - 1) out[n] = (Tout)(off + run);
+  for (int i = 0; i < kScanItems; ++i) o[i] = (Tout)(off + v[i]);
+  if (base + kScanItems <= n && ((reinterpret_cast<uintptr_t>(out + base) & 15u) == 0)) {
+    // whole and aligned: 16-byte stores
+    uint4* d = reinterpret_cast<uint4*>(out + base);
+#pragma unroll
+    for (int i = 0; i < (int)(kScanItems * sizeof(Tout) / 16); ++i) {
+      uint4 q;
+      memcpy(&q, reinterpret_cast<const char*>(o) + 16 * i, 16);
+      d[i] = q;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+      if (base + i < n) out[base + i] = o[i];
   }
+  if (base <= n - 1 && n - 1 < base + kScanItems) out[n] = (Tout)(off + run);
   if (n == 0 && tile == 0 && threadIdx.x == 0) out[0] = (Tout)0;
 }
 
