@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
   __shared__ uint32_t s_whist[kSortWarps][kRadix];
   __shared__ uint32_t s_dstart[kRadix];   // tile-local start of each digit
   __shared__ uint32_t s_gbase[kRadix];    // global start of each digit's slice of this tile
+  __shared__ uint32_t s_wsum[kSortWarps]; // per-warp sums of the digit totals
   __shared__ long long s_tile;
 
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -240,16 +241,22 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
       acc += t;
     }
     total = acc;
-    s_dstart[d] = total;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t acc = 0;
-    for (int d = 0; d < kRadix; ++d) {
-      uint32_t t = s_dstart[d];
-      s_dstart[d] = acc;
-      acc += t;
+  // tile-local start of each digit: block-wide exclusive scan of the digit
+  // totals (thread d holds digit d)
+  {
+    uint32_t incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += y;
     }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) add += w < (int)warp ? s_wsum[w] : 0u;
+    s_dstart[threadIdx.x] = add + incl - total;
   }
   // decoupled look-back per digit (thread d owns digit d)
   {
