@@ -683,10 +683,10 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
 // r2u (a superset of every point with d2 <= r2u, hence of the k nearest),
 // computes their binary64 values and sorts them by (d2, id).  More than
 // KB_CAP such candidates send the query to the ring-by-ring path.
-constexpr int KB_CAP = 1024;
+constexpr int KB_CAP = 512;  // a power of two: the sort pads the list to one
 constexpr int KB_WARPS = 4;
 
-__global__ void __launch_bounds__(KB_WARPS * 32) knn_bounded_kernel(IndexView ix, QuerySet qs,
+__global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView ix, QuerySet qs,
                                                                      const Thresholds* __restrict__ thr_p, int k,
                                                                      const uint32_t* __restrict__ bslot,
                                                                      const float* __restrict__ br2,
@@ -1007,7 +1007,7 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
   f.join();
   {
     ProfScope prof("knn_bounded", st);
-    knn_bounded_kernel<<<sms * 4, KB_WARPS * 32, 0, st>>>(iv, qs, thr, k, bslot, br2, ctrs + 9, idx, d2, slow, ctrs,
+    knn_bounded_kernel<<<sms * 7, KB_WARPS * 32, 0, st>>>(iv, qs, thr, k, bslot, br2, ctrs + 9, idx, d2, slow, ctrs,
                                                           status);
     note_launch();
   }
