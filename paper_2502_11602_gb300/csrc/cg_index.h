@@ -74,10 +74,11 @@ struct RadiusState {
   char thr_host[64];
   // fast kernels: per-group plans, mask / id layouts and the large groups
   struct BlockPlan* plans = nullptr;
-  uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
+  uint32_t *msize = nullptr, *isize = nullptr;
+  int64_t *moff = nullptr, *idoff = nullptr;  // exclusive scans of msize / isize (64-bit)
   uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr;
   uint32_t big_n = 0;
-  uint32_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
+  int64_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
 };
 
 // Mutable state of queries against an index: the external query plan, the
@@ -104,10 +105,12 @@ struct RadiusWork {
   Thresholds* thr = nullptr;
   void *scan_scr = nullptr, *plan_scr = nullptr;
   struct BlockPlan* plans = nullptr;
-  uint32_t *msize = nullptr, *isize = nullptr, *moff = nullptr, *idoff = nullptr;
+  uint32_t *msize = nullptr, *isize = nullptr;
+  int64_t *moff = nullptr, *idoff = nullptr;
   uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr;
   int32_t* row_scratch = nullptr;
-  uint32_t cap_nb = 0, cap_m = 0, cap_i = 0;
+  uint32_t cap_nb = 0;
+  int64_t cap_m = 0, cap_i = 0;
   uint64_t cap_scr = 0;
   int64_t cap_out = 0;
 };

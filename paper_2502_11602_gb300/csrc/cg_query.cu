@@ -549,8 +549,8 @@ __global__ void replay_thresholds_kernel(Thresholds* out, const Tile* __restrict
 
 // capacity checks of a replayed pass: new data that outgrows a buffer
 // stops the rest of the run (every later kernel tests ST_REPLAN first)
-__global__ void replay_check_plan_kernel(const uint32_t* __restrict__ moff_end, uint32_t cap_m,
-                                         const uint32_t* __restrict__ idoff_end, uint32_t cap_i, uint32_t* status) {
+__global__ void replay_check_plan_kernel(const int64_t* __restrict__ moff_end, int64_t cap_m,
+                                         const int64_t* __restrict__ idoff_end, int64_t cap_i, uint32_t* status) {
   if (*moff_end > cap_m || *idoff_end > cap_i) atomicOr(status, ST_REPLAN);
 }
 __global__ void replay_check_out_kernel(const int64_t* __restrict__ total, int64_t cap_out,
@@ -784,8 +784,8 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       R.plans = (BlockPlan*)R.bufs.get(sizeof(BlockPlan) * (size_t)nb, st);
       R.msize = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
       R.isize = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
-      R.moff = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
-      R.idoff = (uint32_t*)R.bufs.get(4 * (size_t)(nb + 1), st);
+      R.moff = (int64_t*)R.bufs.get(8 * (size_t)(nb + 1), st);
+      R.idoff = (int64_t*)R.bufs.get(8 * (size_t)(nb + 1), st);
       R.big_list = (uint32_t*)R.bufs.get(4 * (size_t)nb, st);
       void* sscr = R.bufs.get(scan_scratch_bytes(nb), st);
       if (!R.plans || !R.msize || !R.isize || !R.moff || !R.idoff || !R.big_list || !sscr)
@@ -793,19 +793,23 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       Lbig.qs.blk_list = R.big_list;
       e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
                              R.ctrs + 12, C.status, st);
-      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.msize, R.moff, nb, sscr, C.status, st);
-      if (e == cudaSuccess) e = exclusive_scan_u32_u32(R.isize, R.idoff, nb, sscr, C.status, st);
-      uint32_t tots[3] = {0, 0, 0};
+      // 64-bit offsets: a call's mask words may exceed 2^32 (hundreds of
+      // millions of queries with wide candidate sets)
+      if (e == cudaSuccess) e = exclusive_scan_u32_i64(R.msize, R.moff, nb, sscr, C.status, st);
+      if (e == cudaSuccess) e = exclusive_scan_u32_i64(R.isize, R.idoff, nb, sscr, C.status, st);
+      int64_t tots[2] = {0, 0};
+      uint32_t nbig = 0;
       HostRead rd;
-      rd.get(&tots[0], R.moff + nb, 4);
-      rd.get(&tots[1], R.idoff + nb, 4);
-      rd.get(&tots[2], R.ctrs + 12, 4);
+      rd.get(&tots[0], R.moff + nb, 8);
+      rd.get(&tots[1], R.idoff + nb, 8);
+      rd.get(&nbig, R.ctrs + 12, 4);
       if (e == cudaSuccess) e = rd.sync(st);
       if (e != cudaSuccess) return cuda_fail(e, "radius plan");
-      R.masks = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[0], 1), st);
-      R.ids = (uint32_t*)R.bufs.get(4 * (size_t)std::max<uint32_t>(tots[1], 1), st);
+      if (tots[0] < 0 || tots[1] < 0) return fail(CG_ERR_INTERNAL, "radius plan: negative buffer size");
+      R.masks = (uint32_t*)R.bufs.get(4 * (size_t)std::max<int64_t>(tots[0], 1), st);
+      R.ids = (uint32_t*)R.bufs.get(4 * (size_t)std::max<int64_t>(tots[1], 1), st);
       if (!R.masks || !R.ids) return fail(CG_ERR_OOM, "device allocation failed (radius masks)");
-      R.big_n = tots[2];
+      R.big_n = nbig;
       R.mtot = tots[0];
       R.itot = tots[1];
       {
@@ -915,8 +919,8 @@ cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double
   const int64_t n = std::max<int64_t>(ix->n, 1);
   auto grow = [&](double v, double slack) { return v * headroom + slack; };
   w.cap_nb = std::max<uint32_t>(cap_nb, 1);
-  w.cap_m = (uint32_t)std::min(grow(R.mtot, 65536.0), 4.0e9);
-  w.cap_i = (uint32_t)std::min(grow(R.itot, 65536.0), 4.0e9);
+  w.cap_m = (int64_t)grow((double)R.mtot, 65536.0);
+  w.cap_i = (int64_t)grow((double)R.itot, 65536.0);
   w.cap_scr = (uint64_t)grow((double)R.heavy_scratch, 1 << 20);
   w.cap_out = (int64_t)grow((double)total, 1 << 20);
   w.counts = (uint32_t*)w.bufs.get(4 * (size_t)n, st);
@@ -929,8 +933,8 @@ cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double
   w.plans = (BlockPlan*)w.bufs.get(sizeof(BlockPlan) * (size_t)w.cap_nb, st);
   w.msize = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
   w.isize = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
-  w.moff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
-  w.idoff = (uint32_t*)w.bufs.get(4 * ((size_t)w.cap_nb + 1), st);
+  w.moff = (int64_t*)w.bufs.get(8 * ((size_t)w.cap_nb + 1), st);
+  w.idoff = (int64_t*)w.bufs.get(8 * ((size_t)w.cap_nb + 1), st);
   w.big_list = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_nb, st);
   w.masks = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_m, st);
   w.ids = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_i, st);
@@ -976,8 +980,8 @@ cg_status radius_replay(cg_index* ix, RadiusWork& w, const uint32_t* nkeys_dev, 
   const uint32_t nb = w.cap_nb;
   e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, w.thr, w.plans, w.msize, w.isize, w.big_list, w.ctrs + 12,
                          ix->status, st);
-  if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.msize, w.moff, nb, w.plan_scr, ix->status, st);
-  if (e == cudaSuccess) e = exclusive_scan_u32_u32(w.isize, w.idoff, nb, w.plan_scr, ix->status, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_i64(w.msize, w.moff, nb, w.plan_scr, ix->status, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_i64(w.isize, w.idoff, nb, w.plan_scr, ix->status, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay plan");
   replay_check_plan_kernel<<<1, 1, 0, st>>>(w.moff + nb, w.cap_m, w.idoff + nb, w.cap_i, ix->status); note_launch();
   {

@@ -127,21 +127,21 @@ cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const Qu
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
                                uint32_t* big_n, const uint32_t* status, cudaStream_t st);
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
-                                 const Thresholds* thr, const BlockPlan* plans, const uint32_t* moff,
-                                 const uint32_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
+                                 const Thresholds* thr, const BlockPlan* plans, const int64_t* moff,
+                                 const int64_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
                                  unsigned* work, uint32_t* status, cudaStream_t st);
 cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
-                                const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                const int64_t* moff, const int64_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                 const uint32_t* status, cudaStream_t st);
 
 // Binary32 records: warp-per-group count and fill for the two size classes.
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
-                                  const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
+                                  const BlockPlan* plans, const int64_t* moff, const int64_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
                                   uint32_t* status, const cudaStream_t* sts);
 cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
-                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                 const int64_t* moff, const int64_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                  const uint32_t* status, const cudaStream_t* sts);
 

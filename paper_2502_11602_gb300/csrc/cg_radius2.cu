@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "cg_f32x2.cuh"
 #include "cg_query.cuh"
 #include "cg_sort.cuh"
 
@@ -62,25 +63,6 @@ __device__ __forceinline__ float ru(const double4_32a& q, const Tile& T, int a) 
 }
 __device__ __forceinline__ float rabs(const float4& q, int a) { return fabsf(a == 0 ? q.x : (a == 1 ? q.y : q.z)); }
 __device__ __forceinline__ float rabs(const double4_32a&, int) { return 0.f; }
-
-template <int KERN>
-__device__ __forceinline__ bool exact_in(const double* __restrict__ p, const double* __restrict__ c, double r2) {
-  double dx = __dsub_rn(__ldg(p), __ldg(c));
-  double dy = __dsub_rn(__ldg(p + 1), __ldg(c + 1));
-  double dz = __dsub_rn(__ldg(p + 2), __ldg(c + 2));
-  if (KERN == CG_SPHERE)
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
-  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
-  return fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
-}
-template <int KERN>
-__device__ __forceinline__ bool exact_in4(const double4_32a& p, const double4_32a& c, double r2) {
-  double dx = __dsub_rn(p.x, c.x), dy = __dsub_rn(p.y, c.y), dz = __dsub_rn(p.z, c.z);
-  if (KERN == CG_SPHERE)
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
-  if (KERN == CG_CYLINDER) return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= r2;
-  return fmax(fmax(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) <= r2;
-}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -277,30 +259,6 @@ __device__ void cta_sort_by_id(const R* A, R* B, int K, int passes, uint16_t* hi
   }
 }
 
-__device__ __forceinline__ unsigned long long pk(float a, float b) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk(unsigned long long r, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
 template <int PREC>
 struct CountSmem;
 template <>
@@ -315,8 +273,8 @@ template <int PREC, int KERN>
 __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySet qs,
                                                            const Thresholds* __restrict__ thr_p,
                                                            const BlockPlan* __restrict__ plans,
-                                                           const uint32_t* __restrict__ moff,
-                                                           const uint32_t* __restrict__ idoff,
+                                                           const int64_t* __restrict__ moff,
+                                                           const int64_t* __restrict__ idoff,
                                                            uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ masks,
                                                            uint32_t* __restrict__ ids, unsigned* work,
@@ -402,7 +360,7 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
     }
     for (uint32_t t = threadIdx.x; t < nq; t += CT) cnt_s[t] = 0;
     uint32_t* mb = masks + moff[b];
-    const uint32_t io = idoff[b];
+    const size_t io = (size_t)idoff[b];
     // binary64 records: the exact predicate directly
     R* recB = reinterpret_cast<R*>(Bmem);
     if (K > 0)
@@ -469,36 +427,6 @@ struct C5 {
   __host__ __device__ static constexpr size_t per_slot(int) { return (R1 + SLOT + RUNS + 15) / 16 * 16; }
 };
 
-// The binary32 values of a candidate pair (packed): squared distance for the
-// sphere, its xy part for the cylinder, largest squared axis offset for the
-// cube.
-template <int KERN>
-__device__ __forceinline__ unsigned long long pair_vals(const ulonglong2& xy, unsigned long long zz,
-                                                        unsigned long long QX, unsigned long long QY,
-                                                        unsigned long long QZ) {
-  const unsigned long long DX = sub2(xy.x, QX), DY = sub2(xy.y, QY);
-  if (KERN == CG_CYLINDER) return fma2(DY, DY, mul2(DX, DX));
-  const unsigned long long DZ = sub2(zz, QZ);
-  if (KERN == CG_SPHERE) return fma2(DZ, DZ, fma2(DY, DY, mul2(DX, DX)));
-  float a0, a1, b0, b1, c0, c1;
-  upk(mul2(DX, DX), a0, a1);
-  upk(mul2(DY, DY), b0, b1);
-  upk(mul2(DZ, DZ), c0, c1);
-  return pk(fmaxf(fmaxf(a0, b0), c0), fmaxf(fmaxf(a1, b1), c1));
-}
-template <int KERN>
-__device__ __forceinline__ void pair_test(const ulonglong2& xy, unsigned long long zz, unsigned long long QX,
-                                          unsigned long long QY, unsigned long long QZ, float& v0, float& v1) {
-  upk(pair_vals<KERN>(xy, zz, QX, QY, QZ), v0, v1);
-}
-
-// m << 1 with the sign bit of x shifted in (one funnel shift).
-__device__ __forceinline__ uint32_t push_sign(uint32_t m, float x) {
-  uint32_t d;
-  asm("shf.l.wrap.b32 %0, %1, %2, 1;" : "=r"(d) : "r"(__float_as_uint(x)), "r"(m));
-  return d;
-}
-
 // Hit masks of one 32-candidate word against one query: bit j of *in is set
 // when the binary32 value of candidate j is <= lo, bit j of *hi when it is
 // <= hi.  TL = pk(T_lo, T_lo) with T_lo the next binary32 above lo (0 when
@@ -531,12 +459,6 @@ __device__ __forceinline__ void word_masks(const ulonglong2* __restrict__ xyw, c
   hi = (mh[3] << 24) | (mh[2] << 16) | (mh[1] << 8) | mh[0];
 }
 
-// The comparison constants of word_masks for a threshold t (t < FLT_MAX).
-__device__ __forceinline__ unsigned long long above(float t) {
-  const float T = t < 0.f ? 0.f : __uint_as_float(__float_as_uint(t) + 1u);
-  return pk(T, T);
-}
-
 // GW warps share a group (a slot of the CTA): they stage and sort its
 // candidates together (per-slot named barriers), then each takes its own
 // chunks of 32 queries.  GW = 1 for the smallest size class.
@@ -550,8 +472,8 @@ template <int KERN, int KC, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix, QuerySet qs,
                                                                    const Thresholds* __restrict__ thr_p,
                                                                    const BlockPlan* __restrict__ plans,
-                                                                   const uint32_t* __restrict__ moff,
-                                                                   const uint32_t* __restrict__ idoff,
+                                                                   const int64_t* __restrict__ moff,
+                                                                   const int64_t* __restrict__ idoff,
                                                                    uint32_t* __restrict__ counts,
                                                                    uint32_t* __restrict__ masks,
                                                                    uint32_t* __restrict__ ids, unsigned* work,
@@ -603,7 +525,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
       continue;
     }
     uint32_t* mb = masks + moff[b];
-    const uint32_t io = idoff[b];
+    const size_t io = (size_t)idoff[b];
     const uint32_t Wp = (K + 31u) / 32u;
     // runs and their offsets in the run-order concatenation
     if (wis == 0) {
@@ -794,8 +716,8 @@ struct F5 {
 template <int KC, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, QuerySet qs,
                                                                   const BlockPlan* __restrict__ plans,
-                                                                  const uint32_t* __restrict__ moff,
-                                                                  const uint32_t* __restrict__ idoff,
+                                                                  const int64_t* __restrict__ moff,
+                                                                  const int64_t* __restrict__ idoff,
                                                                   const uint32_t* __restrict__ masks,
                                                                   const uint32_t* __restrict__ ids,
                                                                   const int64_t* __restrict__ offsets,
@@ -827,7 +749,7 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
     const uint32_t heavy = __ldg(hp + 4), gcls = __ldg(hp + 5);
     if (heavy || gcls != cls || nq == 0 || K == 0) continue;
     const uint32_t Wp = (K + 31u) / 32u;
-    const uint32_t io = idoff[b];
+    const size_t io = (size_t)idoff[b];
     const uint32_t* __restrict__ mb = masks + moff[b];
     for (uint32_t j = tis; j < K; j += ST) sids[j] = __ldg(ids + io + j);
     slot_sync<GW>(slot);
@@ -921,8 +843,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_fill5_kernel(IndexView ix, 
 template <int PREC>
 __global__ void __launch_bounds__(CT) radius_fill2_kernel(IndexView ix, QuerySet qs,
                                                           const BlockPlan* __restrict__ plans,
-                                                          const uint32_t* __restrict__ moff,
-                                                          const uint32_t* __restrict__ idoff,
+                                                          const int64_t* __restrict__ moff,
+                                                          const int64_t* __restrict__ idoff,
                                                           const uint32_t* __restrict__ masks,
                                                           const uint32_t* __restrict__ ids,
                                                           const int64_t* __restrict__ offsets,
@@ -952,7 +874,7 @@ __global__ void __launch_bounds__(CT) radius_fill2_kernel(IndexView ix, QuerySet
     const uint32_t q0 = s_hdr[0], nq = s_hdr[1], K = s_hdr[2];
     const uint32_t W = s_hdr[3] >> 16, heavy = s_hdr[4];
     if (heavy || nq == 0 || K == 0) continue;
-    const uint32_t io = idoff[b];
+    const size_t io = (size_t)idoff[b];
     const uint32_t* __restrict__ mb = masks + moff[b];
     for (uint32_t j = threadIdx.x; j < K; j += CT) sids[j] = ids[io + j];
     for (uint32_t t = threadIdx.x; t < nq; t += CT) soff[t] = offsets[rid(qsrc[q0 + t])];
@@ -1037,8 +959,8 @@ cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const Qu
 }
 
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
-                                 const Thresholds* thr, const BlockPlan* plans, const uint32_t* moff,
-                                 const uint32_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
+                                 const Thresholds* thr, const BlockPlan* plans, const int64_t* moff,
+                                 const int64_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
                                  unsigned* work, uint32_t* status, cudaStream_t st) {
   int bits = 1;
   while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)iv.n) ++bits;
@@ -1063,7 +985,7 @@ cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const 
 }
 
 cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
-                                const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                const int64_t* moff, const int64_t* idoff, const uint32_t* masks,
                                 const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                 const uint32_t* status, cudaStream_t st) {
   ProfScope prof("radius_fill2", st);
@@ -1075,7 +997,7 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
 }
 
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
-                                  const BlockPlan* plans, const uint32_t* moff, const uint32_t* idoff,
+                                  const BlockPlan* plans, const int64_t* moff, const int64_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
                                   uint32_t* status, const cudaStream_t* sts) {
   // size classes: K <= 512 (a warp per group, 7 warps per CTA), <= 1024
@@ -1114,7 +1036,7 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
 }
 
 cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
-                                 const uint32_t* moff, const uint32_t* idoff, const uint32_t* masks,
+                                 const int64_t* moff, const int64_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                  const uint32_t* status, const cudaStream_t* sts) {
 #define CG_F5(KC, NW, GW, CLS, WORK)                                                              \
