@@ -32,6 +32,7 @@ _lib = None
 
 DENSE, SPARSE, MIXED = 0, 1, 2
 SPHERE, CUBE, CYLINDER = 0, 1, 2
+GROW_MONOTONE, GROW_DENSITY = 0, 1
 
 _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 
@@ -78,6 +79,7 @@ def _load():
             "og_radius_count_mt": (None, [P, P, I64, D, I, P, I]),
             "og_radius_fill_mt": (None, [P, P, I64, D, I, P, P, I]),
             "og_knn_mt": (None, [P, P, I64, I64, P, P, I]),
+            "og_knn_policy_mt": (None, [P, P, I64, I64, I, P, P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -214,6 +216,18 @@ class Index:
         else:
             _load().og_knn_mt(self._h, _ptr(q), q.shape[0], k, _ptr(idx), _ptr(dd), threads)
         return idx, dd
+
+    def knn_policy(self, q, k: int, policy: int = GROW_MONOTONE, threads: int = 1):
+        """Algorithm 2 under a growth policy (GROW_MONOTONE: r + s;
+        GROW_DENSITY: the density step of Section 3.4.2): (idx, d2, visited)
+        with visited[i] the voxels of query i's final taboo box."""
+        q = _pts(q)
+        idx = np.empty((q.shape[0], k), np.int32)
+        dd = np.empty((q.shape[0], k), np.float64)
+        vis = np.empty(q.shape[0], np.int64)
+        _load().og_knn_policy_mt(self._h, _ptr(q), q.shape[0], k, int(policy), _ptr(idx), _ptr(dd), _ptr(vis),
+                                 max(1, threads))
+        return idx, dd, vis
 
 
 def brute_radius(xyz, c, r: float, kernel: int = SPHERE) -> np.ndarray:

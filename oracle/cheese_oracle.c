@@ -49,6 +49,11 @@
 #define OG_SPHERE 0
 #define OG_CUBE 1
 #define OG_CYLINDER 2
+#define OG_GROW_MONOTONE 0
+#define OG_GROW_DENSITY 1
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* predicates                                                                */
@@ -441,13 +446,27 @@ static int og_cand_cmp(const void* a, const void* b) {
  *    their points to the candidate set;
  *  - P^ = candidates with d(p, c) <= r, compared as d2 <= fl(r*r);
  *  - the loop ends when |P^| >= k or T covers G; otherwise r grows.
- * Growth: the monotone step r + s of Algorithm 2.  The density-based step is
- * garbled in the paper (two different formulas) and changes only the number
- * of iterations, never the result, so the oracle uses the monotone step.
- * When T covers G with |P^| < k, every point is a candidate and the k
- * nearest candidates are returned (N < k: all N).
+ * Growth (policy):
+ *  OG_GROW_MONOTONE  r + s, s the smallest voxel side (the first phase of
+ *                    Section 3.4.2, used throughout);
+ *  OG_GROW_DENSITY   Algorithm 2's second phase: with P^ non-empty, the
+ *                    density rho = |P^| / ((4/3) pi r^3) of the ball gives
+ *                    the radius whose ball holds k points at that density,
+ *                    r = (3 k / (4 pi rho))^(1/3) (the paper prints this
+ *                    step without the 3 / (4 pi) of the ball volume, and once
+ *                    with rho and k swapped; the reading here keeps the
+ *                    ball's volume, which the density's own definition uses);
+ *                    with P^ empty, or |P^| the same as in the previous
+ *                    iteration (the density did not change), r + s.
+ * The policy changes only the sequence of radii, never the result: the loop
+ * stops only when every point within r has been collected and at least k of
+ * them are within r.  When T covers G with |P^| < k, every point is a
+ * candidate and the k nearest candidates are returned (N < k: all N).
+ * *visited (if non-NULL) receives |T|, the number of voxels of the final
+ * taboo box (Section 3.5: the voxels the search explored).
  */
-void og_knn_one(const og_index* ix, const double* c, int64_t k, int32_t* idx, double* d2o) {
+void og_knn_one_policy(const og_index* ix, const double* c, int64_t k, int policy, int32_t* idx,
+                       double* d2o, int64_t* visited) {
   int64_t n = ix->n;
   og_cand* cand = (og_cand*)malloc(sizeof(og_cand) * (size_t)n);
   if (!cand) return;
@@ -476,7 +495,7 @@ void og_knn_one(const og_index* ix, const double* c, int64_t k, int32_t* idx, do
 
   int have_T = 0;
   int64_t T0[3] = {0, 0, 0}, T1[3] = {-1, -1, -1};
-  int64_t inside = 0;
+  int64_t inside = 0, inside_prev = -1;
   for (;;) {
     int64_t b0[3] = {0, 0, 0}, b1[3] = {0, 0, 0};
     int empty = 0;
@@ -510,7 +529,18 @@ void og_knn_one(const og_index* ix, const double* c, int64_t k, int32_t* idx, do
     for (int a = 0; a < nax; ++a)
       if (T0[a] != 0 || T1[a] != ix->nc[a] - 1) covers = 0;
     if (inside >= k || covers) break;
-    r = r + s_min;
+    if (policy == OG_GROW_DENSITY && inside > 0 && inside != inside_prev) {
+      double rho = (double)inside / ((4.0 / 3.0) * M_PI * r * r * r);
+      r = cbrt(3.0 * (double)k / (4.0 * M_PI * rho));
+    } else {
+      r = r + s_min;
+    }
+    inside_prev = inside;
+  }
+  if (visited) {
+    int64_t v = 1;
+    for (int a = 0; a < 3; ++a) v *= have_T ? (T1[a] - T0[a] + 1) : 0;
+    *visited = v;
   }
   qsort(cand, (size_t)ncand, sizeof(og_cand), og_cand_cmp);
   for (int64_t t = 0; t < k; ++t) {
@@ -518,6 +548,10 @@ void og_knn_one(const og_index* ix, const double* c, int64_t k, int32_t* idx, do
     else { idx[t] = -1; d2o[t] = INFINITY; }
   }
   free(cand);
+}
+
+void og_knn_one(const og_index* ix, const double* c, int64_t k, int32_t* idx, double* d2o) {
+  og_knn_one_policy(ix, c, k, OG_GROW_MONOTONE, idx, d2o, NULL);
 }
 
 void og_knn(const og_index* ix, const double* q, int64_t nq, int64_t k, int32_t* idx, double* d2) {
@@ -557,7 +591,7 @@ void og_brute_knn_one(const double* xyz, int64_t n, const double* c, int64_t k,
 typedef struct {
   const og_index* ix; const double* q; int64_t q0, q1; double r; int kernel; int64_t k;
   int64_t* counts; const int64_t* offsets; int32_t* indices; int32_t* kidx; double* kd2;
-  int mode;
+  int mode; int policy; int64_t* visited;
 } og_job;
 
 static void* og_worker(void* arg) {
@@ -575,7 +609,8 @@ static void* og_worker(void* arg) {
     free(tmp);
   } else {
     for (int64_t t = jb->q0; t < jb->q1; ++t)
-      og_knn_one(jb->ix, jb->q + 3 * t, jb->k, jb->kidx + jb->k * t, jb->kd2 + jb->k * t);
+      og_knn_one_policy(jb->ix, jb->q + 3 * t, jb->k, jb->policy, jb->kidx + jb->k * t, jb->kd2 + jb->k * t,
+                        jb->visited ? jb->visited + t : NULL);
   }
   return NULL;
 }
@@ -620,5 +655,13 @@ void og_knn_mt(const og_index* ix, const double* q, int64_t nq, int64_t k, int32
                double* d2, int nthreads) {
   og_job b; memset(&b, 0, sizeof b);
   b.ix = ix; b.q = q; b.k = k; b.kidx = idx; b.kd2 = d2; b.mode = 2;
+  og_run(b, nq, nthreads);
+}
+
+/* k-NN under a growth policy, with the voxels each search visited. */
+void og_knn_policy_mt(const og_index* ix, const double* q, int64_t nq, int64_t k, int policy, int32_t* idx,
+                      double* d2, int64_t* visited, int nthreads) {
+  og_job b; memset(&b, 0, sizeof b);
+  b.ix = ix; b.q = q; b.k = k; b.kidx = idx; b.kd2 = d2; b.mode = 2; b.policy = policy; b.visited = visited;
   og_run(b, nq, nthreads);
 }
