@@ -159,6 +159,40 @@ def _sum_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def _tile_config(n: int, precision: str, world: int) -> dict:
+    """The tile workload's config (the same dict on both arms)."""
+    return {"workload": "ALS tile 12M pts, 500x500 m, 2D dense grid 1 m, sphere r=1 m, all points as queries",
+            "n_points": n, "radius_m": RADIUS, "cell_m": CELL, "precision": precision,
+            "l2": "inputs larger than L2 (288 MB points, 129 MB L2)", "parallelism": f"replicas x{world}"}
+
+
+def _single_core(xyz, sample_queries: int, seed: int = 6) -> dict:
+    """The oracle on one thread: the whole small ALS tile (100k points, every
+    point a query, r = 1 m) and a seeded 1 % query sample of the large tile,
+    extrapolated to every point as a query (labelled as such)."""
+    import numpy as np
+
+    import cloudgen
+    import oracle
+    small = cloudgen.als_uniform()
+    t0 = time.perf_counter()
+    six = oracle.Index(small, CELL)
+    six.radius_search(small, RADIUS, oracle.SPHERE, threads=1)
+    t_small = time.perf_counter() - t0
+    ix = oracle.Index(xyz, CELL)
+    q = xyz[np.random.default_rng(seed).integers(0, len(xyz), sample_queries)]
+    t0 = time.perf_counter()
+    ix.radius_search(q, RADIUS, oracle.SPHERE, threads=1)
+    t_q = time.perf_counter() - t0
+    return {"cores": 1,
+            "small_tile_queries_per_s": len(small) / t_small,
+            "small_tile": f"{len(small)} points, build + every point a query, one thread ({t_small:.2f} s)",
+            "large_tile_sample_queries_per_s": sample_queries / t_q,
+            "large_tile_sample": f"{sample_queries} seeded random queries of the {len(xyz)}-point tile "
+                                 f"(1 %), one thread ({t_q:.2f} s); queries only, extrapolation: "
+                                 f"{len(xyz) / (sample_queries / t_q):.0f} s for every point as a query"}
+
+
 def _cpu_baseline(xyz, sample_queries: int, seed: int = 5):
     """The oracle as it stands, on the host cores: full single-threaded build
     plus a seeded sample of queries on all cores, extrapolated to N queries."""
@@ -179,7 +213,8 @@ def _cpu_baseline(xyz, sample_queries: int, seed: int = 5):
             "sample": f"full single-threaded oracle build of the {len(xyz)}-point tile ({t_build:.1f} s) + "
                       f"{sample_queries} seeded random queries on {cores} threads ({t_q:.1f} s), "
                       f"query time extrapolated to all {len(xyz)} queries",
-            "build_s": t_build, "query_sample_s": t_q}
+            "build_s": t_build, "query_sample_s": t_q,
+            "single_core": _single_core(xyz, len(xyz) // 100)}
 
 
 def run_reference(args):
@@ -208,16 +243,21 @@ def run_reference(args):
         if step >= args.warmup:
             times.append(dt)
     t_q = statistics.mean(times)
-    t_step = t_build + t_q * len(xyz) / S  # one full step: build + every point a query
-    value = len(xyz) / t_step
+    # the timed region: each step is one sample of S queries (count + fill,
+    # rows sorted) against the resident oracle index
+    value = S / t_q
+    t_full = t_build + t_q * len(xyz) / S  # a whole step, extrapolated (labelled below)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_q * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "ALS tile 12M pts, 500x500 m, 2D dense grid 1 m, sphere r=1 m, all points as queries",
-                       "n_points": len(xyz), "radius_m": RADIUS, "cell_m": CELL},
+            "config": _tile_config(len(xyz), args.precision, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"oracle build of the full tile once ({t_build:.1f} s, 1 thread); each step "
-                                       f"{S} seeded random queries on {cores} threads, extrapolated to all queries"},
+                             "sample": f"each step: {S} seeded random queries of the {len(xyz)}-point tile on "
+                                       f"{cores} threads against the oracle index built once before the timed "
+                                       f"region ({t_build:.1f} s, one thread); value = sample queries / step time"},
+            "extrapolated_full_step": {"ms": t_full * 1e3, "queries_per_s": len(xyz) / t_full,
+                                       "how": "oracle build + the sample's per-query time x every point as a query "
+                                              "(not timed as one region)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -481,9 +521,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == cg.FP32_OFFSET else "f64", "data": "synthetic",
-        "config": {"workload": "ALS tile 12M pts, 500x500 m, 2D dense grid 1 m, sphere r=1 m, all points as queries",
-                   "n_points": n, "radius_m": RADIUS, "cell_m": CELL, "precision": args.precision,
-                   "l2": "inputs larger than L2 (288 MB points, 129 MB L2)", "parallelism": f"replicas x{world}"},
+        "config": _tile_config(n, args.precision, world),
         "neighbors_per_s": total_all / (ms * 1e-3), "neighbors_per_step": total_all,
         "stages_ms": {"build": build_ms, "count": count_ms, "fill": fill_ms},
         "kernels_ms_per_step": per_step,
@@ -524,13 +562,17 @@ def run_batched(args):
     xyz, off = cloudgen.batched_tiles(args.tiles, args.batch_points, seed=cloudgen.CONFIG_SEED + 3 + 1000 * rank)
     n = len(xyz)
     x = torch.from_numpy(xyz).to(dev)
-    cells, report = autotune.tune(xyz, off, radius=1.0, k=16, precision=cg.FP32_OFFSET,
-                                  cache_path=os.path.join(ROOT, "_build", "autotune.json"))
+    cache = os.path.join(ROOT, "_build", "autotune.json")
+    cells, report = autotune.tune(xyz, off, radius=1.0, k=16, precision=cg.FP32_OFFSET, cache_path=cache)
+    tuning, launch_report = autotune.tune_launch(xyz, off, cells, radius=1.0, precision=cg.FP32_OFFSET,
+                                                 cache_path=cache)
     out = {}
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(1.0)
-    for name, prec in (("fp32", cg.FP32_OFFSET), ("fp64", cg.FP64)):
+    for name, prec, tun in (("fp32", cg.FP32_OFFSET, tuning), ("fp32_default_shapes", cg.FP32_OFFSET, None),
+                            ("fp64", cg.FP64, None)):
+        cg.cg_set_tuning(tun)  # launch shapes are fixed when the pipeline's graph is captured
         pipe = cg.Pipeline(x, off, cells, radius=1.0, k=16, precision=prec)
         for _ in range(args.warmup):
             total = pipe.run()
@@ -550,6 +592,10 @@ def run_batched(args):
         assert pipe.info()["replans"] == 0
         ms = _max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
         info = pipe.info()
+        if name == "fp32_default_shapes":
+            out[name] = {"ms_per_step": ms, "queries_per_s": world * n / (ms * 1e-3)}
+            pipe.close()
+            continue
         # end to end: pinned host points in, CSR and k-NN out, every step
         host_in = torch.from_numpy(xyz).pin_memory()
         outs = pipe.outputs()
@@ -579,6 +625,7 @@ def run_batched(args):
         pipe.close()
         del host_in, host, outs, o
     clk = clocks.stop()
+    cg.cg_set_tuning(None)
     f = out["fp32"]
     line = {
         "metric": "batched radius+kNN queries/s (256 ALS tiles, ~60M pts, r=1 m, k=16, one graph replay per step)",
@@ -589,8 +636,12 @@ def run_batched(args):
                                "10k-2M, 2D dense grids, cell autotuned per density bucket, sphere r=1 m, k=16",
                    "n_points": n, "tiles": args.tiles, "cells_used": sorted(set(cells.tolist())),
                    "autotune_report": {str(k): v for k, v in report.items()},
+                   "launch_tuning": tuning,
+                   "launch_tuning_report": {str(k): v for k, v in launch_report.items()},
                    "l2": "inputs larger than L2 (1.4 GB points)"},
         "fp32_offset": f, "fp64": out["fp64"],
+        "fp32_default_shapes": out["fp32_default_shapes"],
+        "tuned_over_default_shapes": out["fp32_default_shapes"]["ms_per_step"] / f["ms_per_step"],
         "fp32_over_fp64": out["fp64"]["ms_per_step"] / f["ms_per_step"],
         "e2e": {"value": f["e2e_queries_per_s"], "unit": "queries/s", "h2d_bytes_per_step": n * 24,
                 "d2h_bytes_per_step": f["d2h_bytes"]},
@@ -784,17 +835,72 @@ def run_memory(args):
                 torch.cuda.synchronize()
                 t_build = time.perf_counter() - t0
                 info = ix.info()
-                # records (16 n) + exact copy (24 n) are point data; the rest indexes them
-                tables = info["device_bytes"] - 40 * n
+                # records (16 n) + exact copy (24 n) are point data, and so is
+                # the height-sorted copy of 2D grids (16 n + 4 n ids); the rest
+                # indexes them
+                zcopy = 20 * n if dim == 2 else 0
+                tables = info["device_bytes"] - 40 * n - zcopy
                 rows.append({"dim": dim, "cell_m": cell, "flavor": names[fl], "ncell": info["ncell"],
                              "nonempty": info["nonempty"], "device_MiB": info["device_bytes"] / 2 ** 20,
                              "index_MiB": tables / 2 ** 20, "index_over_8n": tables / (8.0 * n),
+                             "height_copy_MiB": zcopy / 2 ** 20,
                              "build_ms": t_build * 1e3})
                 ix.close()
     line = {"metric": "index device memory vs the 8 n-byte minimum (12M ALS tile)", "value": None,
             "unit": "MiB", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": "12M ALS tile; index bytes = device bytes minus the 16 n B binary32 records "
                                    "and the 24 n B exact copy", "n_points": n, "min_8n_MiB": 8 * n / 2 ** 20},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_sz(args):
+    """Slice thickness of the 3D mixed flavour (Section 3.3.3) on the street
+    canyon cloud: the z voxel side s_z swept at a fixed 0.25 m xy side; per
+    setting the build time, device memory, dense slices, and the radius
+    (r = 0.1 m, count + fill) and k-NN (k = 16) times on 1M of the cloud's
+    points as queries; the binary64 results are identical in every setting."""
+    import numpy as np
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    n = args.points if args.points != N_POINTS else 20_000_000
+    xyz = cloudgen.tls_street(n)
+    x = torch.from_numpy(xyz).to(dev)
+    q = torch.from_numpy(cloudgen.sample_queries(xyz, 1_000_000, seed=cloudgen.CONFIG_SEED + 2)).to(dev)
+    rows, ref = [], None
+    for sz in (0.125, 0.25, 0.5, 1.0, 2.0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ix = cg.Index(x, 0.25, sz, dim=3, flavor=cg.MIXED)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        info = ix.info()
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b), out
+        t_rad, (off, ind) = timed(lambda: ix.radius_search(q, 0.1))
+        t_knn, (kidx, _) = timed(lambda: ix.knn(q, 16))
+        sig = (int(off[-1]), int(ind.sum()), int(kidx.sum()))
+        ref = ref or sig
+        rows.append({"s_z_m": sz, "slices": info["nslices"], "dense_slices": info["dense_slices"],
+                     "nonempty": info["nonempty"], "device_MiB": info["device_bytes"] / 2 ** 20,
+                     "build_ms": t_build * 1e3, "radius_ms": t_rad, "knn16_ms": t_knn, "same_result": sig == ref})
+        ix.close()
+    line = {"metric": "3D mixed flavour: slice thickness s_z sweep (street canyon cloud)", "value": None,
+            "unit": "ms", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"TLS street canyon {n} pts, 3D mixed, xy voxel 0.25 m, 1M queries drawn "
+                                   "from the cloud, sphere r = 0.1 m and k = 16", "n_points": n},
             "rows": rows}
     print(json.dumps(line), flush=True)
 
@@ -811,7 +917,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS, help="tile size (profiling cases only)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison on the tile")
-    ap.add_argument("--workload", choices=["tile", "batched", "serving", "latency", "memory"], default="tile")
+    ap.add_argument("--workload", choices=["tile", "batched", "serving", "latency", "memory", "sz"], default="tile")
     ap.add_argument("--tiles", type=int, default=256)
     ap.add_argument("--batch-points", type=int, default=60_000_000)
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -830,6 +936,8 @@ def main():
         run_serving(args)
     elif args.workload == "latency":
         run_latency(args)
+    elif args.workload == "sz":
+        run_sz(args)
     elif args.workload == "memory":
         run_memory(args)
     else:

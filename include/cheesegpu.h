@@ -163,7 +163,9 @@ cg_status cg_index_free(cg_index_t index);
  * voxels' points, predicate).  Writes offsets[0..nq] = exclusive prefix sum
  * of the per-query neighbour counts (offsets[0] = 0, offsets[nq] = total).
  *  q_dev        device float64 [nq][3] query centres (any position).
- *  nq           >= 0.  r > 0 finite.  kernel  CG_SPHERE or CG_CUBE.
+ *  nq           >= 0.  r > 0 finite.  kernel  CG_SPHERE, CG_CUBE or
+ *               CG_CYLINDER (Section 2's kernels; the cylinder is vertical,
+ *               z unbounded).
  *  offsets_dev  device int64 [nq+1], written.
  *  total_host   if non-NULL receives the total; the call then synchronises.
  * Queries keep an internal plan (query order, blocks) that cg_radius_fill
@@ -184,10 +186,13 @@ cg_status cg_radius_fill(cg_index_t index, const double* q_dev, int64_t nq, doub
                          void* stream);
 
 /*
- * cg_radius_search -- count + scan + fill with outputs allocated by the
+ * cg_radius_search -- both passes of the kernel search of Algorithm 1
+ * (Section 3.4.1): count + scan + fill, with outputs allocated by the
  * library (hook or cudaMallocAsync); the caller releases them with
- * cg_free_device (or its own hook).  Synchronises the stream once (the
- * total sizes the output).
+ * cg_free_device (or its own hook).  Arguments and errors as
+ * cg_radius_count / cg_radius_fill; *offsets_dev, *indices_dev and *total
+ * are written only on CG_OK.  Synchronises the stream once (the total sizes
+ * the output).
  */
 cg_status cg_radius_search(cg_index_t index, const double* q_dev, int64_t nq, double r,
                            cg_kernel kernel, int64_t** offsets_dev, int32_t** indices_dev,
@@ -197,9 +202,12 @@ cg_status cg_radius_search(cg_index_t index, const double* q_dev, int64_t nq, do
 cg_status cg_free_device(void* ptr, void* stream);
 
 /*
- * Queries that are the indexed points themselves (every point a query, no
- * copy of the queries): same outputs as the calls above with q = the points
- * in original order, nq = n.
+ * cg_all_points_count / cg_all_points_fill -- Algorithm 1 (Section 3.4.1)
+ * with every indexed point as a query (the queries are the index's own
+ * points, no copy of them is made): the same outputs as cg_radius_count /
+ * cg_radius_fill with q = the points in original order and nq = n, so row i
+ * holds the neighbours of point i, ascending, point i included.  Errors as
+ * those calls; the fill must follow a count with the same r and kernel.
  */
 cg_status cg_all_points_count(cg_index_t index, double r, cg_kernel kernel, int64_t* offsets_dev,
                               int64_t* total_host, void* stream);
@@ -222,6 +230,31 @@ cg_status cg_all_points_knn(cg_index_t index, int32_t k, int32_t* idx_dev, doubl
                             void* stream);
 
 /*
+ * cg_knn_grow -- Algorithm 2 (Section 3.4.2) run step by step for each
+ * query, one search per query: the radius r starts at the distance from c
+ * to the nearest wall of its voxel; each iteration visits the voxels of the
+ * bounding box of B(c, r) (widened by one voxel per side) outside the taboo
+ * box of Section 3.5, and the search stops when at least k candidates lie
+ * within r or every voxel has been visited.  The growth of r:
+ *   policy 0  r + s (s the smallest voxel side), the monotone step;
+ *   policy 1  the density step of the second phase: with the candidates
+ *             within r non-empty and their number changed since the previous
+ *             iteration, r = (3 k / (4 pi rho))^(1/3) with rho their number
+ *             over the ball's volume (4/3) pi r^3; otherwise r + s.
+ * The result does not depend on the policy and equals cg_knn's; the policy
+ * changes how many voxels a search explores (Section 3.5 compares them).
+ *  q_dev        device float64 [nq][3].   1 <= k <= 64.
+ *  idx_dev      device int32 [nq][k], d2_dev float64 [nq][k] or NULL: as cg_knn.
+ *  visited_dev  device int64 [nq] or NULL: voxels of each search's final
+ *               taboo box.
+ * CG_ERR_INVALID for k or policy out of range; CG_ERR_UNIMPLEMENTED on a
+ * batched index.  Non-finite query coordinates are reported by
+ * cg_index_status (that query's row is padding).  Asynchronous on `stream`.
+ */
+cg_status cg_knn_grow(cg_index_t index, const double* q_dev, int64_t nq, int32_t k, int32_t policy,
+                      int32_t* idx_dev, double* d2_dev, int64_t* visited_dev, void* stream);
+
+/*
  * cg_offsets_scan_noalloc -- the exclusive scan that turns per-query
  * neighbour counts into CSR offsets, without allocating any device memory.
  * The paper has no counterpart: this entry point exists for callers that
@@ -237,8 +270,11 @@ cg_status cg_all_points_knn(cg_index_t index, int32_t k, int32_t* idx_dev, doubl
  *  offsets_dev  device int64 [n+1], written: offsets[0] = 0,
  *               offsets[i+1] = offsets[i] + counts[i].  If a bounded device
  *               wait gives up, offsets[n] is set to -1 (the other entries are
- *               then unreliable); this never happens unless the GPU is shared
- *               so heavily that a resident block cannot make progress.
+ *               then unreliable) and the call has still returned CG_OK (it
+ *               returns before the kernel runs): a caller that must be sure
+ *               reads offsets[n] after the stream completes and checks that
+ *               it is >= 0.  A wait gives up only if the GPU is shared so
+ *               heavily that a resident block cannot make progress.
  *  stream       the call is asynchronous on this stream.
  * Scratch: 512 KiB + 256 B in a file-scope device array that every GPU which
  * loads the library holds until the process exits.  It is shared by all
@@ -431,6 +467,30 @@ cg_status cg_server_free(cg_server_t server);
  */
 cg_status cg_profile_enable(int on);
 cg_status cg_profile_read(char* buf, size_t cap, size_t* len, int reset);
+
+/*
+ * Launch tuning of the radius search (process-wide; the autotuner's knobs).
+ * They change only speed, never a result.
+ *  radius_chunk_height  all-points passes on binary32 2D grids: the height
+ *                       span of a voxel group's chunk, in radii (> 0;
+ *                       default 8).
+ *  radius_chunk_max     queries per chunk (1 .. 512; default 256).
+ *  count_shape          launch shape of the count kernels' three size
+ *                       classes (0 default, 1, 2): warps per CTA and warps
+ *                       sharing a voxel group.
+ *  fill_shape           the same for the fill kernels.
+ * cg_set_tuning(NULL) restores the defaults; out-of-range fields give
+ * CG_ERR_INVALID and change nothing.  Calls already queued keep the settings
+ * they were issued with; a captured pipeline keeps those of its capture.
+ */
+typedef struct {
+  float radius_chunk_height;
+  uint32_t radius_chunk_max;
+  int32_t count_shape;
+  int32_t fill_shape;
+} cg_tuning_t;
+cg_status cg_set_tuning(const cg_tuning_t* tuning);
+cg_status cg_get_tuning(cg_tuning_t* tuning);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ from . import _build
 DENSE, SPARSE, MIXED = 0, 1, 2
 SPHERE, CUBE, CYLINDER = 0, 1, 2
 FP64, FP32_OFFSET = 0, 1
+GROW_MONOTONE, GROW_DENSITY = 0, 1
 
 STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4: "CG_ERR_TIMEOUT",
           5: "CG_ERR_OVERFLOW", 6: "CG_ERR_INTERNAL", 7: "CG_ERR_UNIMPLEMENTED"}
@@ -30,10 +31,10 @@ STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4:
 EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count", "cg_build", "cg_build_batched",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
            "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
-           "cg_all_points_knn", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
+           "cg_all_points_knn", "cg_knn_grow", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
            "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free", "cg_server_create", "cg_server_submit",
            "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free",
-           "cg_profile_enable", "cg_profile_read"]
+           "cg_profile_enable", "cg_profile_read", "cg_set_tuning", "cg_get_tuning"]
 
 REQ_RADIUS, REQ_KNN = 0, 1
 
@@ -52,6 +53,29 @@ class IndexInfo(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("nc", ctypes.c_int64 * 3),
                 ("cell", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
                 ("enc_err", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("radius_chunk_height", ctypes.c_float), ("radius_chunk_max", ctypes.c_uint32),
+                ("count_shape", ctypes.c_int32), ("fill_shape", ctypes.c_int32)]
+
+
+def cg_set_tuning(tuning: dict | None = None):
+    """Process-wide launch tuning (None restores the defaults); keys as
+    cg_tuning_t: radius_chunk_height, radius_chunk_max, count_shape, fill_shape."""
+    if tuning is None:
+        _check(load().cg_set_tuning(None))
+        return
+    t = Tuning(**cg_get_tuning())
+    for k, v in tuning.items():
+        setattr(t, k, v)
+    _check(load().cg_set_tuning(ctypes.byref(t)))
+
+
+def cg_get_tuning() -> dict:
+    t = Tuning()
+    _check(load().cg_get_tuning(ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
 class PipelineOpts(ctypes.Structure):
@@ -129,6 +153,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_all_points_fill": [P, D, I, P, P, P],
             "cg_knn": [P, P, I64, I32, P, P, P],
             "cg_all_points_knn": [P, I32, P, P, P],
+            "cg_knn_grow": [P, P, I64, I32, I32, P, P, P, P],
             "cg_offsets_scan_noalloc": [P, I64, P, P],
             "cg_pipeline_create": [P, P, I32, P, I, I, P, P, P],
             "cg_pipeline_run": [P, P, P],
@@ -144,6 +169,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_server_free": [P],
             "cg_profile_enable": [I],
             "cg_profile_read": [P, ctypes.c_size_t, P, I],
+            "cg_set_tuning": [P],
+            "cg_get_tuning": [P],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -256,6 +283,11 @@ def cg_all_points_fill(h, r, kernel, offsets, indices, stream=None):
 
 def cg_knn(h, q, k, idx, d2=None, stream=None):
     _check(load().cg_knn(h, _ptr(q), q.shape[0], int(k), _ptr(idx), _ptr(d2), _stream(stream)))
+
+
+def cg_knn_grow(h, q, k, policy, idx, d2=None, visited=None, stream=None):
+    _check(load().cg_knn_grow(h, _ptr(q), q.shape[0], int(k), int(policy), _ptr(idx), _ptr(d2), _ptr(visited),
+                              _stream(stream)))
 
 
 def cg_all_points_knn(h, k, idx, d2=None, stream=None):
@@ -533,6 +565,18 @@ class Index:
         if check:
             cg_index_status(self.h, stream)
         return offsets, indices[:total]
+
+    def knn_grow(self, q: torch.Tensor, k: int, policy: int = GROW_MONOTONE, stream=None, check: bool = True):
+        """Algorithm 2 step by step under a growth policy: (idx, d2, visited)."""
+        q = _points(q)
+        nq = q.shape[0]
+        idx = torch.empty((nq, k), dtype=torch.int32, device=self.device)
+        d2 = torch.empty((nq, k), dtype=torch.float64, device=self.device)
+        vis = torch.empty(nq, dtype=torch.int64, device=self.device)
+        cg_knn_grow(self.h, q, k, policy, idx, d2, vis, stream=stream)
+        if check:
+            cg_index_status(self.h, stream)
+        return idx, d2, vis
 
     def knn(self, q: torch.Tensor | None, k: int, with_d2: bool = True, stream=None,
             check: bool = True):

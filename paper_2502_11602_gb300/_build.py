@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcheesegpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["cg_sort.cu", "cg_build.cu", "cg_query.cu", "cg_radius2.cu", "cg_knn.cu", "cg_capi.cu", "cg_noalloc.cu", "cg_pipeline.cu", "cg_server.cu"]
+SOURCES = ["cg_sort.cu", "cg_build.cu", "cg_query.cu", "cg_radius2.cu", "cg_zwin.cu", "cg_small.cu", "cg_knn.cu", "cg_capi.cu", "cg_noalloc.cu", "cg_pipeline.cu", "cg_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -1,4 +1,4 @@
-"""Cell-size autotuner for batched tiles.
+"""Autotuner for batched tiles: cell size, chunk height and launch shapes.
 
 Tiles are grouped by point density (points per m^2 of their xy bounding box,
 one bucket per factor of two).  For every bucket not yet in the cache, one
@@ -99,3 +99,98 @@ def tune(xyz: np.ndarray, tile_offsets, radius: float, kernel: int = 0, k: int =
         os.replace(tmp, cache_path)
     cells = np.array([cache[_key(gpu, dim, radius, kernel, k, precision, int(b))] for b in buckets])
     return cells, report
+
+
+# ------------------------------------------------------------ launch shapes
+#
+# The radius kernels' launch shapes (warps per CTA and warps sharing a voxel
+# group, per size class) and the height span of an all-points chunk (binary32
+# 2D grids) are this design's "threads per query" and "staging depth": they
+# set how many lanes share a group's staged candidates and how many queries
+# one staging serves.  Like the cell size they change only speed.
+
+CHUNK_HEIGHTS = (4.0, 8.0, 12.0)
+SHAPES = (0, 1, 2)
+
+
+def _time_radius(cg, ix, radius: float, kernel: int, reps: int = 3) -> float:
+    times = []
+    for it in range(reps + 1):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        ix.radius_search(None, radius, kernel, check=False)
+        b.record()
+        torch.cuda.synchronize()
+        if it > 0:
+            times.append(a.elapsed_time(b))
+    return float(np.median(times))
+
+
+def tune_launch(xyz: np.ndarray, tile_offsets, cells, radius: float, kernel: int = 0, dim: int = 2,
+                precision: int = 1, cache_path: str | None = None, device: str = "cuda:0") -> tuple[dict, dict]:
+    """Launch tuning per density bucket (coordinate descent: chunk height,
+    then the count kernels' shape, then the fill kernels'), each bucket's
+    median tile searched at its cell size; cached like the cell sizes.
+    Returns the tuning of the bucket holding the most points (one tuning
+    serves a whole batch, whose tiles share each launch) and a report
+    {bucket: {"tuning": ..., "ms": {setting: ms}}} of the buckets measured."""
+    import paper_2502_11602_gb300 as cg
+
+    off = np.asarray(tile_offsets, dtype=np.int64)
+    T = len(off) - 1
+    cells = np.asarray(cells, dtype=np.float64)
+    cache_path = cache_path or default_cache_path()
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    gpu = torch.cuda.get_device_name(torch.device(device))
+    buckets = np.array([density_bucket(xyz[off[t]:off[t + 1]]) for t in range(T)])
+    saved = cg.cg_get_tuning()
+    report = {}
+    try:
+        for bk in sorted(set(buckets.tolist())):
+            key = _key(gpu, dim, radius, kernel, 0, precision, bk) + "|launch"
+            if key in cache:
+                continue
+            members = np.nonzero(buckets == bk)[0]
+            sizes = off[members + 1] - off[members]
+            rep = int(members[np.argsort(sizes)[len(sizes) // 2]])
+            tile = torch.from_numpy(np.ascontiguousarray(xyz[off[rep]:off[rep + 1]])).to(device)
+            ix = cg.Index(tile, float(cells[rep]), float(cells[rep]), dim=dim, precision=precision)
+            best = {"radius_chunk_height": 8.0, "count_shape": 0, "fill_shape": 0}
+            ms = {}
+
+            def trial(**kw):
+                t = dict(best, **kw)
+                cg.cg_set_tuning(t)
+                v = _time_radius(cg, ix, radius, kernel)
+                ms[",".join(f"{k}={t[k]:g}" for k in sorted(t))] = v
+                return v
+
+            chunked = dim == 2 and precision == 1 and kernel in (0, 1)
+            for field, values in (("radius_chunk_height", CHUNK_HEIGHTS if chunked else (8.0,)),
+                                  ("count_shape", SHAPES), ("fill_shape", SHAPES)):
+                times = {v: trial(**{field: v}) for v in values}
+                best[field] = min(times, key=times.get)
+            ix.close()
+            del tile
+            cache[key] = best
+            report[bk] = {"tuning": dict(best), "ms": ms, "tile": rep, "points": int(off[rep + 1] - off[rep])}
+    finally:
+        cg.cg_set_tuning(saved)
+    if report:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    pts = {}
+    for t in range(T):
+        pts[int(buckets[t])] = pts.get(int(buckets[t]), 0) + int(off[t + 1] - off[t])
+    main = max(pts, key=pts.get)
+    batch = dict(cache[_key(gpu, dim, radius, kernel, 0, precision, main) + "|launch"])
+    return batch, report

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "cg_index.h"
+#include "cg_query.cuh"
 #include "cg_sort.cuh"
 
 namespace cg {
@@ -518,6 +519,15 @@ cg_status build_index(const double* xyz, int64_t n, const int64_t* toff_host, in
   CG_CUDA(cudaGetLastError());
   CG_CUDA(cudaMemsetAsync(ix->scratch_u32, 0, 4, st));
   max_run_kernel<<<grid_for(m, kThreads, 152 * 4), kThreads, 0, st>>>(ix->ustart, m, ix->scratch_u32); note_launch();
+  if (precision == CG_FP32_OFFSET && dim == 2) {
+    // every voxel run again, sorted by height (the radius kernels' z windows)
+    uint32_t* zlong;
+    CG_ALLOC(ix->pts32z, float4, n, ix->bufs);
+    CG_ALLOC(ix->sidz, uint32_t, n, ix->bufs);
+    CG_ALLOC(zlong, uint32_t, m + 1, tmp);
+    CG_CUDA(launch_zsort(ix->pts32, ix->pts32z, ix->sidz, ix->ustart, m, nullptr, (uint32_t)n, zlong, zlong + m,
+                         ix->status, st));
+  }
 
   if (flavor == CG_DENSE) {
     uint32_t* cnt;
@@ -603,8 +613,9 @@ cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st) {
   w.cap_keys = (uint32_t)std::min<int64_t>(n, ix->ncell);
   w.ukeys = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_keys, st);
   w.ustart = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_keys + 4, st);
+  if (ix->pts32z) w.zlong = (uint32_t*)w.bufs.get(4 * (size_t)w.cap_keys + 4, st);
   if (!w.keys || !w.skeys || !w.flag || !w.rank || !w.cnt || !w.sort_scr || !w.scan_scr || !w.bb || !w.toff ||
-      !w.ukeys || !w.ustart)
+      !w.ukeys || !w.ustart || (ix->pts32z && !w.zlong))
     return fail(CG_ERR_OOM, "device allocation failed (pipeline build work)");
   std::vector<int64_t> toff(ix->ntiles + 1);
   for (int t = 0; t < ix->ntiles; ++t) toff[t] = ix->tiles_host[t].pt_base;
@@ -648,6 +659,11 @@ cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream
   if (e != cudaSuccess) return cuda_fail(e, "replay scan");
   run_emit_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(w.skeys, n, w.flag, w.rank, ix->ukeys, ix->ustart,
                                                                w.cap_keys); note_launch();
+  if (ix->pts32z) {
+    e = launch_zsort(ix->pts32, ix->pts32z, ix->sidz, ix->ustart, w.cap_keys, w.nkeys_dev, (uint32_t)n, w.zlong,
+                     w.zlong + w.cap_keys, ix->status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "replay height sort");
+  }
   e = cudaMemsetAsync(w.cnt, 0, 4 * (size_t)ix->ncell, st);
   if (e != cudaSuccess) return cuda_fail(e, "replay memset");
   voxel_count_dev_kernel<<<grid_for(w.cap_keys, kThreads), kThreads, 0, st>>>(ix->ukeys, ix->ustart, w.nkeys_dev,

@@ -437,6 +437,27 @@ const char* cg_version(void) { return "cheesegpu 0.1 (sm_103a)"; }
 
 uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+cg_status cg_set_tuning(const cg_tuning_t* t) {
+  cg_tuning_t v = default_tuning();
+  if (t) {
+    if (!(t->radius_chunk_height > 0.f) || !isfinite(t->radius_chunk_height))
+      return fail(CG_ERR_INVALID, "radius_chunk_height must be positive and finite");
+    if (t->radius_chunk_max < 1 || t->radius_chunk_max > 512)
+      return fail(CG_ERR_INVALID, "radius_chunk_max must be in [1, 512]");
+    if (t->count_shape < 0 || t->count_shape > 2 || t->fill_shape < 0 || t->fill_shape > 2)
+      return fail(CG_ERR_INVALID, "count_shape and fill_shape must be 0, 1 or 2");
+    v = *t;
+  }
+  set_tuning(v);
+  return CG_OK;
+}
+
+cg_status cg_get_tuning(cg_tuning_t* t) {
+  if (!t) return fail(CG_ERR_INVALID, "NULL argument");
+  *t = current_tuning();
+  return CG_OK;
+}
+
 cg_status cg_profile_enable(int on) {
   if (!on) prof_resolve();
   g_prof_on.store(on != 0);
@@ -607,6 +628,12 @@ cg_status cg_all_points_knn(cg_index_t ix, int32_t k, int32_t* idx_dev, double* 
                             void* stream) {
   if (!ix || !idx_dev) return fail(CG_ERR_INVALID, "NULL argument");
   return knn_pass(ix, true, nullptr, ix->n, k, idx_dev, d2_dev, (cudaStream_t)stream);
+}
+
+cg_status cg_knn_grow(cg_index_t ix, const double* q_dev, int64_t nq, int32_t k, int32_t policy,
+                      int32_t* idx_dev, double* d2_dev, int64_t* visited_dev, void* stream) {
+  if (!ix || !idx_dev || (nq > 0 && !q_dev)) return fail(CG_ERR_INVALID, "NULL argument");
+  return knn_grow_pass(ix, q_dev, nq, k, policy, idx_dev, d2_dev, visited_dev, (cudaStream_t)stream);
 }
 
 }  // extern "C"

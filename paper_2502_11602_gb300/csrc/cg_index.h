@@ -79,6 +79,10 @@ struct RadiusState {
   uint32_t *masks = nullptr, *ids = nullptr, *big_list = nullptr;
   uint32_t big_n = 0;
   int64_t mtot = 0, itot = 0;  // mask words / staged ids of the last count
+  // all-points groups cut into height chunks (height-sorted columns)
+  uint32_t *zbeg = nullptr, *zkey = nullptr;
+  uint32_t znb = 0;
+  bool small = false;  // the count took the small-batch path (so does the fill)
 };
 
 // Mutable state of queries against an index: the external query plan, the
@@ -134,6 +138,7 @@ struct BuildWork {
   const uint32_t* nkeys_dev = nullptr;           // non-empty voxels of the last replay
   uint32_t cap_keys = 0;
   int bits = 0;
+  uint32_t* zlong = nullptr;  // [cap_keys + 1]: long runs of the height sort, then their count
 };
 
 }  // namespace cg
@@ -146,6 +151,8 @@ struct cg_index {
   cg::DevBufs bufs;
   cg::Tile* tiles = nullptr;
   float4* pts32 = nullptr;
+  float4* pts32z = nullptr;      // binary32 2D grids: every voxel run sorted by height
+  uint32_t* sidz = nullptr;      // [n] original id of every position of pts32z
   double4_32a* pts64s = nullptr;
   double* xyz64 = nullptr;
   uint32_t* ukeys = nullptr;
@@ -175,6 +182,7 @@ struct cg_index {
     v.n = (uint32_t)n;
     v.nkeys = nkeys;
     v.pts32 = pts32;
+    v.pts32z = pts32z;
     v.pts64s = pts64s;
     v.sid = sid;
     v.xyz64 = xyz64;
@@ -198,11 +206,17 @@ cg_status check_status_word(uint32_t* status, cudaStream_t st);
 // device word on an error).
 cg_status status_verdict(uint32_t w, uint32_t* status, cudaStream_t st);
 cg_status prepare_queries(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, bool reuse, cudaStream_t st);
+cg_status make_zchunks(cg_index* ix, float dz, uint32_t qmax, DevBufs& bufs, uint32_t* status, cudaStream_t st,
+                       uint32_t** cbeg, uint32_t** ckey, uint32_t* nchunks);
 cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
                       cudaStream_t st);
 cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
                    double* d2, cudaStream_t st);
+// Algorithm 2 step by step under a growth policy (0 monotone, 1 density),
+// with the voxels each search visited (cg_knn.cu).
+cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
+                        int64_t* visited, cudaStream_t st, uint32_t* status = nullptr);
 cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
 cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
 cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,

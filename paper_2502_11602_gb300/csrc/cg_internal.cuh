@@ -185,6 +185,7 @@ struct IndexView {
   uint32_t n;              // points
   uint32_t nkeys;          // non-empty voxels (runs)
   const float4* pts32;     // [n] sorted: x~, y~, z~, id bits (binary32 path)
+  const float4* pts32z;    // [n] the same runs, each sorted by z~ (binary32 2D grids), or null
   const double4_32a* pts64s;   // [n] sorted: x, y, z, id bits (binary64 path)
   const double* xyz64;     // [n][3] original order (exact rechecks)
   const uint32_t* sid;     // [n] original id of every sorted position

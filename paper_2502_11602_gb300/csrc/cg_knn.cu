@@ -927,6 +927,137 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
   }
 }
 
+// Algorithm 2 step by step (Section 3.4.2), one warp per query: the radius r
+// in binary64, each iteration visiting the voxels of the bounding box of
+// B(c, r) (widened by one voxel on each side and clamped, as the kernel
+// search's voxel range) outside the taboo box T of Section 3.5, the k best
+// candidates under (d2, id) in the warp's list, and r grown by the policy:
+//   0 (monotone)  r + s, s the smallest voxel side;
+//   1 (density)   with P^ non-empty and |P^| changed since the previous
+//                 iteration, r = (3 k / (4 pi rho))^(1/3) for the density
+//                 rho = |P^| / ((4/3) pi r^3) of the ball; else r + s.
+// |P^| (the candidates within r) is read off the list: at least k when its
+// k-th entry is within r, else every candidate within r is in the list.  The
+// search ends when |P^| >= k or T covers the grid; visited = |T|.
+template <int PREC>
+__global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
+                                                       int k, int policy, int32_t* __restrict__ out_idx,
+                                                       double* __restrict__ out_d2,
+                                                       long long* __restrict__ visited, uint32_t* status) {
+  const unsigned lane = threadIdx.x & 31u;
+  const Tile& T = ix.tiles[0];
+  const int nax = ix.dim;
+  double smin = fmin(T.s[0], T.s[1]);
+  if (nax == 3) smin = fmin(smin, T.s[2]);
+  const double kPi = 3.14159265358979323846;
+  for (uint32_t e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); e < nq;
+       e += gridDim.x * (blockDim.x / 32)) {
+    const double* c = q + 3 * (size_t)e;
+    const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
+    WarpList L;
+    L.d[0] = L.d[1] = INFINITY;
+    L.id[0] = L.id[1] = 0xffffffffu;
+    long long vis = 0;
+    if (!(isfinite(cx[0]) && isfinite(cx[1]) && isfinite(cx[2]))) {
+      if (lane == 0) atomicOr(status, ST_NONFINITE);
+    } else {
+      // the voxel of c (clamped) and the distance to its nearest wall
+      double r = INFINITY;
+      for (int a = 0; a < nax; ++a) {
+        double v = floor(__ddiv_rn(__dsub_rn(cx[a], T.lo[a]), T.s[a]));
+        v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
+        const double wlo = __dadd_rn(T.lo[a], __dmul_rn(v, T.s[a]));
+        const double whi = __dadd_rn(wlo, T.s[a]);
+        r = fmin(r, fmin(fabs(__dsub_rn(cx[a], wlo)), fabs(__dsub_rn(cx[a], whi))));
+      }
+      bool have_t = false;
+      int t0[3] = {0, 0, 0}, t1[3] = {-1, -1, -1};
+      long long inside_prev = -1;
+      for (;;) {
+        int b0[3], b1[3];
+        bool empty = false;
+        for (int a = 0; a < 3; ++a) {
+          if (a < nax) {
+            const double lo = floor(__ddiv_rn(__dsub_rn(__dsub_rn(cx[a], r), T.lo[a]), T.s[a])) - 1.0;
+            const double hi = floor(__ddiv_rn(__dsub_rn(__dadd_rn(cx[a], r), T.lo[a]), T.s[a])) + 1.0;
+            if (hi < 0.0 || lo > (double)(T.n[a] - 1)) empty = true;
+            b0[a] = lo < 0.0 ? 0 : (int)lo;
+            b1[a] = hi > (double)(T.n[a] - 1) ? T.n[a] - 1 : (int)hi;
+          } else {
+            b0[a] = 0;
+            b1[a] = T.n[a] - 1;
+          }
+        }
+        if (!empty) {
+          for (int i = b0[0]; i <= b1[0]; ++i)
+            for (int j = b0[1]; j <= b1[1]; ++j)
+              for (int kz = b0[2]; kz <= b1[2]; ++kz) {
+                if (have_t && i >= t0[0] && i <= t1[0] && j >= t0[1] && j <= t1[1] && kz >= t0[2] && kz <= t1[2])
+                  continue;  // taboo: visited in an earlier iteration
+                const uint32_t key = T.key_base + (nax == 2 ? (uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j
+                                                            : ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) *
+                                                                      (uint32_t)T.n[2] + (uint32_t)kz);
+                const uint2 sp = voxel_span(ix, T, key);
+                for (uint32_t s0 = sp.x; s0 < sp.y; s0 += 32) {
+                  const uint32_t t = s0 + lane;
+                  double d = INFINITY;
+                  uint32_t id = 0xffffffffu;
+                  if (t < sp.y) {
+                    id = PREC == 1 ? __float_as_uint(ix.pts32[t].w) : (uint32_t)__double_as_longlong(ix.pts64s[t].w);
+                    d = exact_d2(ix.xyz64 + 3 * (size_t)id, c);
+                  }
+                  const double worst = wl_get(L, k - 1);
+                  const uint32_t worst_id = __shfl_sync(0xffffffffu, (k - 1) < 32 ? L.id[0] : L.id[1], (k - 1) & 31);
+                  unsigned cand = __ballot_sync(0xffffffffu, t < sp.y && lt(d, id, worst, worst_id));
+                  while (cand) {
+                    const int src = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    wl_insert(L, __shfl_sync(0xffffffffu, d, src), __shfl_sync(0xffffffffu, id, src), k);
+                  }
+                }
+              }
+          for (int a = 0; a < 3; ++a) {
+            t0[a] = b0[a];
+            t1[a] = b1[a];
+          }
+          have_t = true;
+        }
+        const double r2 = __dmul_rn(r, r);
+        long long inside;
+        if (wl_get(L, k - 1) <= r2) {
+          inside = k;
+        } else {
+          const unsigned m0 = __ballot_sync(0xffffffffu, (int)lane < k && L.d[0] <= r2);
+          const unsigned m1 = __ballot_sync(0xffffffffu, (int)lane + 32 < k && L.d[1] <= r2);
+          inside = __popc(m0) + __popc(m1);
+        }
+        bool covers = have_t;
+        for (int a = 0; a < nax; ++a) covers &= t0[a] == 0 && t1[a] == T.n[a] - 1;
+        if (inside >= k || covers) break;
+        if (policy == 1 && inside > 0 && inside != inside_prev) {
+          const double vol = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0 / 3.0, kPi), r), r), r);
+          const double rho = __ddiv_rn((double)inside, vol);
+          r = cbrt(__ddiv_rn(__dmul_rn(3.0, (double)k), __dmul_rn(__dmul_rn(4.0, kPi), rho)));
+        } else {
+          r = __dadd_rn(r, smin);
+        }
+        inside_prev = inside;
+      }
+      if (have_t) vis = (long long)(t1[0] - t0[0] + 1) * (t1[1] - t0[1] + 1) * (t1[2] - t0[2] + 1);
+    }
+    for (int s = 0; s < k; ++s) {
+      const double d = wl_get(L, s);
+      const uint32_t id = __shfl_sync(0xffffffffu, s < 32 ? L.id[0] : L.id[1], s & 31);
+      if (lane == 0) {
+        const bool ok = d < INFINITY;
+        out_idx[(size_t)e * k + s] = ok ? (int32_t)id : -1;
+        if (out_d2) out_d2[(size_t)e * k + s] = ok ? d : INFINITY;
+      }
+    }
+    if (lane == 0 && visited) visited[e] = vis;
+  }
+}
+
 template <int PREC>
 size_t knn_smem() {
   using R = typename KRec<PREC>::T;
@@ -1020,6 +1151,10 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external k-NN queries on a batched index (every point queries its own tile)");
+  // small batches: one warp per query, Algorithm 2 with the density step
+  // (the same result), no query plan
+  if (!all_points && nq > 0 && nq <= kSmallBatch)
+    return knn_grow_pass(ix, q, nq, k, 1, idx, d2, nullptr, st, C.status);
   if (!all_points) {
     cg_status s = prepare_queries(ix, C, q, nq, false, st);
     if (s != CG_OK) return s;
@@ -1111,6 +1246,34 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   return CG_OK;
 }
 
+
+cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
+                        int64_t* visited, cudaStream_t st, uint32_t* status) {
+  if (!status) status = ix->status;
+  if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
+  if (policy != 0 && policy != 1) return fail(CG_ERR_INVALID, "policy must be 0 (monotone) or 1 (density)");
+  if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
+  if (ix->ntiles != 1) return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
+  if (nq == 0) return CG_OK;
+  const int sms = [] {
+    int dev = 0, m = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+    return m > 0 ? m : 152;
+  }();
+  const int grid = (int)std::min<int64_t>((nq + 3) / 4, (int64_t)sms * 16);
+  ProfScope prof("knn_grow", st);
+  if (ix->precision == CG_FP32_OFFSET)
+    knn_grow_kernel<1><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
+                                             reinterpret_cast<long long*>(visited), status);
+  else
+    knn_grow_kernel<0><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
+                                             reinterpret_cast<long long*>(visited), status);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k-NN growth kernel");
+  return CG_OK;
+}
 
 cg_status knn_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, int k, int32_t* idx, double* d2,
                    cudaStream_t st) {

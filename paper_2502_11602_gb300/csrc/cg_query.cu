@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "cg_query.cuh"
 #include "cg_sort.cuh"
@@ -673,6 +674,48 @@ int radius_grid(int prec) {
 
 }  // namespace
 
+namespace {
+std::mutex g_tuning_mutex;
+cg_tuning_t g_tuning = {kRadiusChunkDz, kRadiusChunkMax, 0, 0};
+}  // namespace
+
+cg_tuning_t default_tuning() { return cg_tuning_t{kRadiusChunkDz, kRadiusChunkMax, 0, 0}; }
+cg_tuning_t current_tuning() {
+  std::lock_guard<std::mutex> lock(g_tuning_mutex);
+  return g_tuning;
+}
+void set_tuning(const cg_tuning_t& t) {
+  std::lock_guard<std::mutex> lock(g_tuning_mutex);
+  g_tuning = t;
+}
+
+// All-points voxel groups cut into height chunks (see cg_zwin.cu): the
+// chunk table lives in `bufs`; one host read of the chunk count.
+cg_status make_zchunks(cg_index* ix, float dz, uint32_t qmax, DevBufs& bufs, uint32_t* status, cudaStream_t st,
+                       uint32_t** cbeg, uint32_t** ckey, uint32_t* nchunks) {
+  const uint32_t nruns = ix->nkeys;
+  uint32_t* cnt = (uint32_t*)bufs.get(4 * (size_t)std::max<uint32_t>(nruns, 1), st);
+  uint32_t* coff = (uint32_t*)bufs.get(4 * ((size_t)nruns + 1), st);
+  void* scr = bufs.get(scan_scratch_bytes(std::max<uint32_t>(nruns, 1)), st);
+  if (!cnt || !coff || !scr) return fail(CG_ERR_OOM, "device allocation failed (height chunks)");
+  cudaError_t e = launch_zchunk_count(ix->pts32z, ix->ustart, nruns, dz, qmax, cnt, st);
+  if (e == cudaSuccess) e = exclusive_scan_u32_u32(cnt, coff, nruns, scr, status, st);
+  uint32_t nch = 0;
+  HostRead rd;
+  rd.get(&nch, coff + nruns, 4);
+  if (e == cudaSuccess) e = rd.sync(st);
+  if (e != cudaSuccess) return cuda_fail(e, "height chunks");
+  uint32_t* b = (uint32_t*)bufs.get(4 * ((size_t)nch + 1), st);
+  uint32_t* k = (uint32_t*)bufs.get(4 * (size_t)std::max<uint32_t>(nch, 1), st);
+  if (!b || !k) return fail(CG_ERR_OOM, "device allocation failed (height chunks)");
+  e = launch_zchunk_emit(ix->pts32z, ix->ustart, ix->ukeys, nruns, dz, qmax, coff, b, k, (uint32_t)ix->n, st);
+  if (e != cudaSuccess) return cuda_fail(e, "height chunks");
+  *cbeg = b;
+  *ckey = k;
+  *nchunks = nch;
+  return CG_OK;
+}
+
 // Radius pass state kept on the index between the count and fill calls.
 cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
@@ -683,6 +726,47 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
   RadiusState& R = C.radius;
+  // small batches: one warp per query, no plan (the count reads its sizes
+  // back, so it is taken only when the caller asks for the total)
+  if (!all_points && ix->ntiles == 1 && nq > 0 && nq <= kSmallBatch && (fill ? R.small : total_host != nullptr)) {
+    if (!fill) {
+      R.bufs.release(st);
+      R.valid = false;
+      R.small = false;
+      uint32_t* counts = (uint32_t*)R.bufs.get(4 * (size_t)nq, st);
+      uint32_t* stats = (uint32_t*)R.bufs.get(64, st);
+      if (!counts || !stats) return fail(CG_ERR_OOM, "device allocation failed (small radius pass)");
+      cudaError_t e = launch_small_count(ix->view(), kernel, q, (uint32_t)nq, r, counts, offsets, stats, C.status, st);
+      uint32_t maxrow = 0, w = 0;
+      HostRead rd;
+      rd.get(total_host, offsets + nq, 8);
+      rd.get(&maxrow, stats, 4);
+      rd.get(&w, C.status, 4);
+      if (e == cudaSuccess) e = rd.sync(st);
+      if (e != cudaSuccess) return cuda_fail(e, "small radius count");
+      cg_status s = status_verdict(w, C.status, st);
+      if (s != CG_OK) return s;
+      if (maxrow <= (uint32_t)kSmallRowCap) {
+        R.small = true;
+        R.valid = true;
+        R.all_points = false;
+        R.q = q;
+        R.nq = nq;
+        R.r = r;
+        R.kernel = kernel;
+        R.plan_version = C.plan.version;
+        return CG_OK;
+      }
+      // a row too long for the warp's buffer: the regular path below
+    } else {
+      if (!R.valid || R.all_points || R.q != q || R.nq != nq || R.r != r || R.kernel != kernel)
+        return fail(CG_ERR_INVALID, "radius fill without a matching count pass");
+      cudaError_t e = launch_small_fill(ix->view(), kernel, q, (uint32_t)nq, r, offsets, out, C.status, st);
+      if (e != cudaSuccess) return cuda_fail(e, "small radius fill");
+      return CG_OK;
+    }
+  }
+  if (!fill) R.small = false;
   if (!all_points) {
     cg_status s = prepare_queries(ix, C, q, nq, fill, st);
     if (s != CG_OK) return s;
@@ -774,6 +858,26 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
     L.qs.nblocks = C.plan.nblocks;
   }
   const int grid = radius_grid(ix->precision);
+  // binary32 2D grids, sphere and cube: candidates (and all-points queries)
+  // come from the height-sorted columns; all-points voxel groups are cut
+  // into height chunks (made by the count pass, kept for its fill)
+  const bool zw = zw_applies(ix, kernel);
+  if (zw) {
+    L.iv.pts32 = ix->pts32z;
+    L.iv.sid = ix->sidz;
+    if (all_points) {
+      if (!fill) {
+        const cg_tuning_t tun = current_tuning();
+        cg_status zs = make_zchunks(ix, tun.radius_chunk_height * (float)r, tun.radius_chunk_max, R.bufs, C.status,
+                                    st, &R.zbeg, &R.zkey, &R.znb);
+        if (zs != CG_OK) return zs;
+      }
+      L.qs.nblocks = R.znb;
+      L.qs.blk_beg = R.zbeg;
+      L.qs.blk_key = R.zkey;
+      L.qs.qrec = ix->pts32z;
+    }
+  }
   if (nqq > 0 && L.qs.nblocks > 0) {
     const uint32_t nb = L.qs.nblocks;
     // groups too large for the fast kernels go through the general CTA kernel
@@ -792,7 +896,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
         return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
       Lbig.qs.blk_list = R.big_list;
       e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
-                             R.ctrs + 12, C.status, st);
+                             R.ctrs + 12, C.status, st, zw);
       // 64-bit offsets: a call's mask words may exceed 2^32 (hundreds of
       // millions of queries with wide candidate sets)
       if (e == cudaSuccess) e = exclusive_scan_u32_i64(R.msize, R.moff, nb, sscr, C.status, st);
@@ -820,7 +924,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
         const cudaStream_t sts[3] = {f[0], f[1], f[2]};
         if (ix->precision == CG_FP32_OFFSET) {
           e = launch_radius_count32(kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts, R.masks,
-                                    R.ids, R.ctrs + 20, C.status, sts);
+                                    R.ids, R.ctrs + 20, C.status, sts, zw);
         } else {
           e = launch_radius_count2(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.moff, R.idoff, R.counts,
                                    R.masks, R.ids, R.ctrs + 14, C.status, f[0]);

@@ -110,6 +110,10 @@ __device__ __forceinline__ uint32_t qs_nblocks(const QuerySet& qs) {
   return qs.nblocks_dev ? min(*qs.nblocks_dev, qs.nblocks) : qs.nblocks;
 }
 
+// Voxel runs up to this length are kept sorted by height in pts32z; longer
+// runs keep id order there (searched whole by the z-window kernels).
+constexpr uint32_t kZsortMax = 2048;
+
 // Per voxel group: what the fast radius kernels need (see cg_radius2.cu).
 constexpr int kPlanSpans = 32;  // non-empty voxel runs per group
 struct BlockPlan {
@@ -123,9 +127,11 @@ struct BlockPlan {
 };
 
 // Fast radius kernels (cg_radius2.cu).
+// zw: candidates come from the height-sorted columns, each column restricted
+// to the group's height range widened by the kernel's half height and pad.
 cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, const uint32_t* status, cudaStream_t st);
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw = false);
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
                                  const Thresholds* thr, const BlockPlan* plans, const int64_t* moff,
                                  const int64_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
@@ -139,11 +145,53 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                   const BlockPlan* plans, const int64_t* moff, const int64_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
-                                  uint32_t* status, const cudaStream_t* sts);
+                                  uint32_t* status, const cudaStream_t* sts, bool zspan = false);
 cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const BlockPlan* plans,
                                  const int64_t* moff, const int64_t* idoff, const uint32_t* masks,
                                  const uint32_t* ids, const int64_t* offsets, int32_t* out, unsigned* work,
                                  const uint32_t* status, const cudaStream_t* sts);
+
+// Height order of the voxel columns and the height chunks of all-points
+// radius passes (cg_zwin.cu): chunks span at most kRadiusChunkDz x r in
+// height and hold at most kRadiusChunkMax queries (the fastest of 2, 4, 8
+// and 16 x r and 128 - 512 queries on the 12M ALS tile at r = 1 m).
+constexpr float kRadiusChunkDz = 8.0f;
+constexpr uint32_t kRadiusChunkMax = 256;
+
+// The process-wide launch tuning (cg_set_tuning; defaults above and shape 0).
+cg_tuning_t default_tuning();
+cg_tuning_t current_tuning();
+void set_tuning(const cg_tuning_t& t);
+// Height sort of every voxel run of `in` into `out` and the ids into
+// `sid_out` (runs [ustart[i], ustart[i+1]) for i < min(*ndev, cap), or < cap
+// when ndev is null; n points).
+cudaError_t launch_zsort(const float4* in, float4* out, uint32_t* sid_out, const uint32_t* ustart, uint32_t cap,
+                         const uint32_t* ndev, uint32_t n, uint32_t* long_list, uint32_t* long_n,
+                         const uint32_t* status, cudaStream_t st);
+// Chunks per run (cnt[nruns]), then, with coff = exclusive scan of cnt,
+// every chunk's first position (cbeg[total + 1], cbeg[total] = n) and key.
+cudaError_t launch_zchunk_count(const float4* pz, const uint32_t* ustart, uint32_t nruns, float dz, uint32_t qmax,
+                                uint32_t* cnt, cudaStream_t st);
+cudaError_t launch_zchunk_emit(const float4* pz, const uint32_t* ustart, const uint32_t* ukeys, uint32_t nruns,
+                               float dz, uint32_t qmax, const uint32_t* coff, uint32_t* cbeg, uint32_t* ckey,
+                               uint32_t n, cudaStream_t st);
+// Whether a radius pass on this index and kernel uses the height-sorted
+// columns (binary32 2D grids; sphere and cube, whose kernels are bounded in z).
+inline bool zw_applies(const cg_index* ix, int kern) {
+  return ix->pts32z != nullptr && ix->precision == CG_FP32_OFFSET && ix->dim == 2 &&
+         (kern == CG_SPHERE || kern == CG_CUBE);
+}
+
+// Small query batches (cg_small.cu): one warp per query, no plan.  Calls of
+// up to kSmallBatch external queries take this path when their rows are at
+// most kSmallRowCap long (checked by the count).
+constexpr int64_t kSmallBatch = 1024;
+constexpr int kSmallRowCap = 2048;
+cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
+                               uint32_t* counts, int64_t* offsets, uint32_t* stats, uint32_t* status,
+                               cudaStream_t st);
+cudaError_t launch_small_fill(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
+                              const int64_t* offsets, int32_t* out, uint32_t* status, cudaStream_t st);
 
 QuerySet query_set(cg_index* ix, const double* q, int64_t nq, bool all_points);
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
                                                          uint32_t* __restrict__ msize,
                                                          uint32_t* __restrict__ isize,
                                                          uint32_t* __restrict__ big_list, uint32_t* big_n,
-                                                         const uint32_t* status, int zfull) {
+                                                         const uint32_t* status, int zfull, int zw) {
   using R = typename R2<PREC>::T;
   constexpr int KW = R2<PREC>::KW;
   if (replan_pending(status)) return;
@@ -95,8 +95,19 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
     const int dim = ix.dim;
     const int dimr = (zfull && dim == 3) ? 2 : dim;  // the cylinder spans every z slice
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    // zw: the group's height range widened by the kernel's half height.  A
+    // kernel point has |dz| <= r for dz = fl64(p_z - c_z) (the sphere's and
+    // the cube's values are at least fl64(dz^2), squaring is monotone), so
+    // |z~_p - z~_c| <= r (1 + 2^-52) + e_p + e_q, e the bound on
+    // |z~ - (z - O)|; rounded up with margin, then applied rounding outward.
+    const float zh = __fadd_ru(__fmul_ru(thr.r_f, 1.000001f), __fmul_ru(fmaxf(T.enc_err, thr.e_q), 2.000001f));
+    float zlo = INFINITY, zhi = -INFINITY;
     for (uint32_t t = lane; t < nq; t += 32) {
       const R q = qsrc[qb0 + t];
+      if (PREC == 1 && zw) {
+        zlo = fminf(zlo, __fsub_rd((float)q.z, zh));
+        zhi = fmaxf(zhi, __fadd_ru((float)q.z, zh));
+      }
       for (int a = 0; a < dimr; ++a) {
         float u = ru(q, T, a);
         float rr = __fmul_ru(__fmul_ru(thr.r_f, T.inv_sf[a]), 1.0000005f);
@@ -123,7 +134,13 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
         hi[a] = T.n[a] - 1;
       }
     }
-    // one run per non-empty voxel of the range (each run is sorted by id)
+    if (PREC == 1 && zw)
+      for (int o = 16; o > 0; o >>= 1) {
+        zlo = fminf(zlo, __shfl_xor_sync(0xffffffffu, zlo, o));
+        zhi = fmaxf(zhi, __shfl_xor_sync(0xffffffffu, zhi, o));
+      }
+    // one run per non-empty voxel of the range (sorted by id; zw: by height,
+    // and only the part within [zlo, zhi])
     const int ni = empty ? 0 : hi[0] - lo[0] + 1, nj = empty ? 0 : hi[1] - lo[1] + 1;
     const int nk = empty ? 0 : (dim == 3 ? hi[2] - lo[2] + 1 : 1);
     const int nvox = ni * nj * nk;
@@ -137,6 +154,22 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
       const uint2 sp = voxel_span(ix, T, key);
       start = sp.x;
       len = sp.y - sp.x;
+      if (PREC == 1 && zw && len > 0 && len <= kZsortMax) {
+        uint32_t a = 0, c = len;  // first height >= zlo
+        while (a < c) {
+          const uint32_t m = (a + c) >> 1;
+          if ((float)pts[start + m].z < zlo) a = m + 1;
+          else c = m;
+        }
+        uint32_t d = a, f = len;  // first height > zhi
+        while (d < f) {
+          const uint32_t m = (d + f) >> 1;
+          if ((float)pts[start + m].z <= zhi) d = m + 1;
+          else f = m;
+        }
+        start += a;
+        len = d - a;
+      }
     }
     const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
     const int nsp = __popc(nonempty);
@@ -423,6 +456,8 @@ struct C5 {
   // 16-bit hit counter per query, two per word: in the slot table, which
   // the tests no longer need
   static_assert(2 * (size_t)QB2 <= SLOT, "query counters overlay the slot table");
+  // the crowded-id radix sort's histogram sits after the phase-1 tables
+  static_assert(PH1 == 8 * (size_t)KC && PH1 + 4 * 256 <= R1, "radix histogram overlay");
   // a slot of gw warps: the group's tables
   __host__ __device__ static constexpr size_t per_slot(int) { return (R1 + SLOT + RUNS + 15) / 16 * 16; }
 };
@@ -468,6 +503,72 @@ __device__ __forceinline__ void slot_sync(int slot) {
   else asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(GW * 32) : "memory");
 }
 
+// Positions [0, K) ordered by ids[position] (one warp; the ids are unique):
+// stable LSD radix sort of id - min(id), 8-bit digits, as many passes as the
+// id range needs, between A (initially the identity) and B; returns the
+// buffer holding the result.  hist: 256 words.
+__device__ uint16_t* warp_order_by_id(uint32_t K, const uint32_t* __restrict__ ids, uint16_t* A, uint16_t* B,
+                                      uint32_t* hist, uint32_t lane) {
+  uint32_t mn = 0xffffffffu, mx = 0u;
+  for (uint32_t e = lane; e < K; e += 32) {
+    A[e] = (uint16_t)e;
+    mn = min(mn, ids[e]);
+    mx = max(mx, ids[e]);
+  }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  __syncwarp();
+  const uint32_t range = mx - mn;
+  const int passes = range == 0u ? 0 : (32 - __clz((int)range) + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t sh = 8u * (uint32_t)p;
+    for (uint32_t i = lane; i < 256u; i += 32) hist[i] = 0u;
+    __syncwarp();
+    for (uint32_t e = lane; e < K; e += 32) atomicAdd(&hist[((ids[A[e]] - mn) >> sh) & 255u], 1u);
+    __syncwarp();
+    {  // exclusive scan of the 256 digit counts, eight per lane
+      uint32_t c[8], s = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = hist[8 * lane + u];
+        s += c[u];
+      }
+      uint32_t incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      uint32_t pre = incl - s;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        hist[8 * lane + u] = pre;
+        pre += c[u];
+      }
+    }
+    __syncwarp();
+    for (uint32_t e0 = 0; e0 < K; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const bool valid = e < K;
+      const uint32_t s = valid ? A[e] : 0u;
+      const uint32_t d = valid ? ((ids[s] - mn) >> sh) & 255u : 256u + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t lt = (uint32_t)__popc(peers & lanemask_lt());
+      const uint32_t at = valid ? hist[d] : 0u;
+      __syncwarp();
+      if (valid) {
+        B[at + lt] = (uint16_t)s;
+        if (lt == 0u) hist[d] = at + (uint32_t)__popc(peers);
+      }
+      __syncwarp();
+    }
+    uint16_t* t = A;
+    A = B;
+    B = t;
+  }
+  return A;
+}
+
 template <int KERN, int KC, int NWARP, int GW>
 __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix, QuerySet qs,
                                                                    const Thresholds* __restrict__ thr_p,
@@ -477,7 +578,8 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
                                                                    uint32_t* __restrict__ counts,
                                                                    uint32_t* __restrict__ masks,
                                                                    uint32_t* __restrict__ ids, unsigned* work,
-                                                                   const uint32_t* status, uint32_t cls) {
+                                                                   const uint32_t* status, uint32_t cls,
+                                                                   int zspan) {
   if (replan_pending(status)) return;
   using L = C5<KC>;
   constexpr int ST = GW * 32;  // threads per slot
@@ -608,6 +710,16 @@ __global__ void __launch_bounds__(NWARP * 32) radius_count5_kernel(IndexView ix,
           }
           order[y] = g;
         }
+      }
+    } else if (zspan) {
+      // ids packed into a narrow range, spans in height order: radix sort
+      // (the first warp of the slot; its histogram in the phase-1 area's
+      // unused tail)
+      if (wis == 0) {
+        uint16_t* res = warp_order_by_id(K, ids_r, order, reinterpret_cast<uint16_t*>(bk),
+                                         reinterpret_cast<uint32_t*>(base + 8 * (size_t)KC), lane);
+        if (res != order)
+          for (uint32_t j = lane; j < K; j += 32) order[j] = res[j];
       }
     } else {
       // ids packed into a narrow range: merge the sorted runs by rank
@@ -946,14 +1058,15 @@ int resident_grid(F kern, int threads, size_t smem) {
 
 cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, const uint32_t* status, cudaStream_t st) {
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw) {
   const int zfull = kern == CG_CYLINDER ? 1 : 0;
   const int grid = (int)std::min<int64_t>((qs.nblocks + 3) / 4 + 1, (int64_t)sm_count() * 16);
   ProfScope prof("radius_plan", st);
   if (prec == CG_FP32_OFFSET)
-    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull);
+    radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull,
+                                               zw ? 1 : 0);
   else
-    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull);
+    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull, 0);
   note_launch();
   return cudaGetLastError();
 }
@@ -999,7 +1112,7 @@ cudaError_t launch_radius_fill2(int prec, const IndexView& iv, const QuerySet& q
 cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                   const BlockPlan* plans, const int64_t* moff, const int64_t* idoff,
                                   uint32_t* counts, uint32_t* masks, uint32_t* ids, unsigned* work,
-                                  uint32_t* status, const cudaStream_t* sts) {
+                                  uint32_t* status, const cudaStream_t* sts, bool zspan) {
   // size classes: K <= 512 (a warp per group, 7 warps per CTA), <= 1024
   // (two warps per group, 16 per CTA), <= 2048 (four, 4 per CTA): shapes
   // measured fastest on the 12M ALS tile; work[0..2] are their group
@@ -1014,23 +1127,34 @@ cudaError_t launch_radius_count32(int kern, const IndexView& iv, const QuerySet&
     cudaStream_t st = sts[CLS];                                                                  \
     ProfScope prof(CLS == 2 ? "radius_count5_2k" : (CLS ? "radius_count5_1k" : "radius_count5_512"), st); \
     kfn<<<g, NW * 32, smem, st>>>(iv, qs, thr, plans, moff, idoff, counts, masks, ids, WORK, status, \
-                                  CLS);                                                           \
+                                  CLS, zspan ? 1 : 0);                                            \
     note_launch();                                                                                \
     if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
-  if (kern == CG_SPHERE) {
-    CG_C5(CG_SPHERE, 512, 7, 1, 0u, work);
-    CG_C5(CG_SPHERE, 1024, 16, 2, 1u, work + 1);
-    CG_C5(CG_SPHERE, 2048, 4, 4, 2u, work + 2);
-  } else if (kern == CG_CYLINDER) {
-    CG_C5(CG_CYLINDER, 512, 7, 1, 0u, work);
-    CG_C5(CG_CYLINDER, 1024, 16, 2, 1u, work + 1);
-    CG_C5(CG_CYLINDER, 2048, 4, 4, 2u, work + 2);
-  } else {
-    CG_C5(CG_CUBE, 512, 7, 1, 0u, work);
-    CG_C5(CG_CUBE, 1024, 16, 2, 1u, work + 1);
-    CG_C5(CG_CUBE, 2048, 4, 4, 2u, work + 2);
-  }
+  // launch shapes (warps per CTA, warps per group) of the three classes:
+  // 0 = (7, 1), (16, 2), (4, 4); 1 = (14, 2), (8, 1), (8, 4); 2 = (8, 1),
+  // (16, 4), (4, 2)
+#define CG_C5_ALL(KN)                                      \
+  do {                                                     \
+    if (shape == 1) {                                      \
+      CG_C5(KN, 512, 14, 2, 0u, work);                     \
+      CG_C5(KN, 1024, 8, 1, 1u, work + 1);                 \
+      CG_C5(KN, 2048, 8, 4, 2u, work + 2);                 \
+    } else if (shape == 2) {                               \
+      CG_C5(KN, 512, 8, 1, 0u, work);                      \
+      CG_C5(KN, 1024, 16, 4, 1u, work + 1);                \
+      CG_C5(KN, 2048, 4, 2, 2u, work + 2);                 \
+    } else {                                               \
+      CG_C5(KN, 512, 7, 1, 0u, work);                      \
+      CG_C5(KN, 1024, 16, 2, 1u, work + 1);                \
+      CG_C5(KN, 2048, 4, 4, 2u, work + 2);                 \
+    }                                                      \
+  } while (0)
+  const int shape = current_tuning().count_shape;
+  if (kern == CG_SPHERE) CG_C5_ALL(CG_SPHERE);
+  else if (kern == CG_CYLINDER) CG_C5_ALL(CG_CYLINDER);
+  else CG_C5_ALL(CG_CUBE);
+#undef CG_C5_ALL
 #undef CG_C5
   return cudaGetLastError();
 }
@@ -1052,11 +1176,23 @@ cudaError_t launch_radius_fill32(const IndexView& iv, const QuerySet& qs, const 
     note_launch();                                                                                \
     if ((le = cudaGetLastError()) != cudaSuccess) return le;                                      \
   } while (0)
-  // a warp per group up to 1024 candidates, two above; 16 / 8 / 4 warps
-  // per CTA (measured fastest on the 12M ALS tile)
-  CG_F5(512, 16, 1, 0u, work);
-  CG_F5(1024, 8, 1, 1u, work + 1);
-  CG_F5(2048, 4, 2, 2u, work + 2);
+  // launch shapes (warps per CTA, warps per group) of the three classes:
+  // 0 = (16, 1), (8, 1), (4, 2) (measured fastest on the 12M ALS tile);
+  // 1 = (8, 1), (8, 2), (8, 4); 2 = (16, 2), (16, 2), (4, 1)
+  const int shape = current_tuning().fill_shape;
+  if (shape == 1) {
+    CG_F5(512, 8, 1, 0u, work);
+    CG_F5(1024, 8, 2, 1u, work + 1);
+    CG_F5(2048, 8, 4, 2u, work + 2);
+  } else if (shape == 2) {
+    CG_F5(512, 16, 2, 0u, work);
+    CG_F5(1024, 16, 2, 1u, work + 1);
+    CG_F5(2048, 4, 1, 2u, work + 2);
+  } else {
+    CG_F5(512, 16, 1, 0u, work);
+    CG_F5(1024, 8, 1, 1u, work + 1);
+    CG_F5(2048, 4, 2, 2u, work + 2);
+  }
 #undef CG_F5
   return cudaGetLastError();
 }

@@ -50,3 +50,52 @@ def test_tuning_run_and_cache(tmp_path):
         assert np.array_equal(g_off[a:b + 1] - g_off[a], o_off)
         assert np.array_equal(g_ind[g_off[a]:g_off[b]], o_ind + a)
     pipe.close()
+
+
+def test_tuning_record_defaults_and_checks():
+    # the launch tuning is host state of the library: no GPU needed
+    import paper_2502_11602_gb300 as cg
+    cg.cg_set_tuning(None)
+    d = cg.cg_get_tuning()
+    assert d == {"radius_chunk_height": 8.0, "radius_chunk_max": 256, "count_shape": 0, "fill_shape": 0}
+    cg.cg_set_tuning({"radius_chunk_height": 4.0, "count_shape": 2, "fill_shape": 1})
+    assert cg.cg_get_tuning() == {"radius_chunk_height": 4.0, "radius_chunk_max": 256, "count_shape": 2,
+                                  "fill_shape": 1}
+    for bad in ({"count_shape": 3}, {"fill_shape": -1}, {"radius_chunk_height": 0.0},
+                {"radius_chunk_max": 0}, {"radius_chunk_max": 513}):
+        with pytest.raises(cg.CheeseError):
+            cg.cg_set_tuning(bad)
+        assert cg.cg_get_tuning()["count_shape"] == 2  # unchanged by a refused call
+    cg.cg_set_tuning(None)
+    assert cg.cg_get_tuning() == d
+
+
+@pytest.mark.gpu
+def test_tuned_launch_shapes_pipeline_matches_oracle(tmp_path):
+    import oracle
+    import paper_2502_11602_gb300 as cg
+    xyz, off = cloudgen.batched_tiles(10, 300_000, seed=9)
+    path = str(tmp_path / "tune.json")
+    cells, _ = autotune.tune(xyz, off, radius=1.0, k=0, cache_path=path)
+    tuning, report = autotune.tune_launch(xyz, off, cells, radius=1.0, cache_path=path)
+    assert report and set(tuning) == {"radius_chunk_height", "count_shape", "fill_shape"}
+    assert tuning["count_shape"] in autotune.SHAPES and tuning["fill_shape"] in autotune.SHAPES
+    tuning2, report2 = autotune.tune_launch(xyz, off, cells, radius=1.0, cache_path=path)
+    assert report2 == {} and tuning2 == tuning
+    saved = cg.cg_get_tuning()
+    cg.cg_set_tuning(tuning)
+    try:
+        pipe = cg.Pipeline(torch.from_numpy(xyz).to("cuda:0"), off, cells, radius=1.0, k=0)
+        pipe.run()
+        out = pipe.outputs()
+        g_off = out["offsets"].cpu().numpy()
+        g_ind = out["indices"].cpu().numpy()
+        pipe.close()
+    finally:
+        cg.cg_set_tuning(saved)
+    for t in (0, 5):
+        a, b = off[t], off[t + 1]
+        ref = oracle.Index(xyz[a:b], cells[t])
+        o_off, o_ind = ref.radius_search(xyz[a:b], 1.0, threads=8)
+        assert np.array_equal(g_off[a:b + 1] - g_off[a], o_off)
+        assert np.array_equal(g_ind[g_off[a]:g_off[b]], o_ind + a)
