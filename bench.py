@@ -489,6 +489,15 @@ def run_ours(args):
 
     # secondary measurements on the same tile: k-NN (k = 16) and the binary64 path
     h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, prec)
+    # the candidate tests the count kernels run (height ranges cut Algorithm
+    # 1's voxel scan), from one count pass
+    _off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cg.cg_all_points_count(h, RADIUS, cg.SPHERE, _off)
+    rstats = cg.cg_radius_stats(h)
+    del _off
+    roof_count["executed_tests"] = rstats["tested_pairs"]
+    roof_count["executed_over_algorithmic"] = rstats["tested_pairs"] / tests if tests else None
+    roof_count["executed_lane_ops_per_s"] = OPS_PER_TEST * rstats["tested_pairs"] / (count_k * 1e-3) / 1e12
     kidx = torch.empty((n, 16), dtype=torch.int32, device=dev)
     kd2 = torch.empty((n, 16), dtype=torch.float64, device=dev)
     kt = []
@@ -564,8 +573,10 @@ def run_batched(args):
     x = torch.from_numpy(xyz).to(dev)
     cache = os.path.join(ROOT, "_build", "autotune.json")
     cells, report = autotune.tune(xyz, off, radius=1.0, k=16, precision=cg.FP32_OFFSET, cache_path=cache)
-    tuning, launch_report = autotune.tune_launch(xyz, off, cells, radius=1.0, precision=cg.FP32_OFFSET,
-                                                 cache_path=cache)
+    # launch shapes for the captured batch, timed on the batch itself
+    shapes, launch_report = autotune.tune_pipeline(x, off, cells, radius=1.0, k=16, precision=cg.FP32_OFFSET,
+                                                   cache_path=cache)
+    tuning = dict(cg.cg_get_tuning(), **shapes)
     out = {}
     clocks = ClockSampler(local)
     clocks.start()
@@ -854,6 +865,57 @@ def run_memory(args):
     print(json.dumps(line), flush=True)
 
 
+def run_knn(args):
+    """All-points k-NN on the 12M tile (every point a query, the k closest
+    under (d2, id), binary64 d2 out) for k = 1 .. 64: device time per pass
+    (CUDA events, mean of `steps` after `warmup`) and, per k, the library's
+    own phase split (the box classes, the bounded search, the ring path)."""
+    import torch
+
+    import cloudgen
+    import paper_2502_11602_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    xyz = cloudgen.als_urban(args.points)
+    n = len(xyz)
+    x = torch.from_numpy(xyz).to(dev)
+    h = cg.cg_build(x, CELL, CELL, 2, cg.DENSE, cg.FP32_OFFSET)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for k in (1, 8, 16, 32, 64):
+        idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((n, k), dtype=torch.float64, device=dev)
+        for _ in range(max(args.warmup, 1)):
+            cg.cg_all_points_knn(h, k, idx, d2)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cg.cg_all_points_knn(h, k, idx, d2)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        cg.cg_index_status(h)
+        cg.cg_profile_enable(True)
+        cg.cg_all_points_knn(h, k, idx, d2)
+        torch.cuda.synchronize()
+        phases = {name: round(ms, 4) for name, (_, ms) in cg.cg_profile_read().items()}
+        cg.cg_profile_enable(False)
+        ms = statistics.mean(ts)
+        rows.append({"k": k, "ms": ms, "queries_per_s": n / (ms * 1e-3), "phases_ms": phases})
+        del idx, d2
+    cg.cg_index_free(h)
+    line = {"metric": "all-points k-NN queries/s (12M ALS tile, every point a query)",
+            "value": rows[2]["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"ALS tile {n} pts, 2D dense grid 1 m, binary32 offsets, k-NN all points",
+                       "n_points": n},
+            "by_k": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_sz(args):
     """Slice thickness of the 3D mixed flavour (Section 3.3.3) on the street
     canyon cloud: the z voxel side s_z swept at a fixed 0.25 m xy side; per
@@ -917,7 +979,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS, help="tile size (profiling cases only)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison on the tile")
-    ap.add_argument("--workload", choices=["tile", "batched", "serving", "latency", "memory", "sz"], default="tile")
+    ap.add_argument("--workload", choices=["tile", "batched", "serving", "latency", "memory", "sz", "knn"], default="tile")
     ap.add_argument("--tiles", type=int, default=256)
     ap.add_argument("--batch-points", type=int, default=60_000_000)
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -936,6 +998,8 @@ def main():
         run_serving(args)
     elif args.workload == "latency":
         run_latency(args)
+    elif args.workload == "knn":
+        run_knn(args)
     elif args.workload == "sz":
         run_sz(args)
     elif args.workload == "memory":

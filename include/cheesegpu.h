@@ -198,6 +198,24 @@ cg_status cg_radius_search(cg_index_t index, const double* q_dev, int64_t nq, do
                            cg_kernel kernel, int64_t** offsets_dev, int32_t** indices_dev,
                            int64_t* total, void* stream);
 
+/*
+ * cg_radius_stats -- work of the index's last planned count pass (the
+ * default query context; small batches are not planned and report zeros):
+ *  tested_pairs    candidate tests the fast count kernels ran: the sum over
+ *                  voxel groups of (staged candidates x queries); Algorithm 1
+ *                  itself tests every point of every voxel a kernel's box
+ *                  meets, which the height ranges of 2D grids cut down;
+ *  general_groups  groups too large for the fast kernels (general kernel);
+ *  groups          voxel groups of an all-points pass on height chunks, else -1.
+ * Synchronises the index's stream.
+ */
+typedef struct {
+  int64_t tested_pairs;
+  int64_t general_groups;
+  int64_t groups;
+} cg_radius_stats_t;
+cg_status cg_radius_stats(cg_index_t index, cg_radius_stats_t* stats);
+
 /* Frees a buffer returned by cg_radius_search (stream-ordered). */
 cg_status cg_free_device(void* ptr, void* stream);
 
@@ -280,9 +298,13 @@ cg_status cg_knn_grow(cg_index_t index, const double* q_dev, int64_t nq, int32_t
  * loads the library holds until the process exits.  It is shared by all
  * calls: calls that overlap on the GPU (other streams, other host threads)
  * race and corrupt each other's result; serialise them.  Each call clears
- * the part it uses before its kernel runs.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current and caches it; make that first call before any stream capture.
+ * the part it uses before its kernel runs.  The array's device address
+ * belongs to the CUDA context that loaded the library: every call made while
+ * its stream is not capturing looks it up again (cudaGetSymbolAddress, with
+ * the calling device current), so a call after a device reset finds the
+ * reloaded array; a call made while its stream is capturing reuses the
+ * address that the last such lookup on the device found, and fails with
+ * CG_ERR_INVALID if there was none.
  * The call makes no cudaMalloc, cudaFree or other allocating call.
  */
 cg_status cg_offsets_scan_noalloc(const uint32_t* counts_dev, int64_t n, int64_t* offsets_dev,

@@ -34,7 +34,7 @@ EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count",
            "cg_all_points_knn", "cg_knn_grow", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
            "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free", "cg_server_create", "cg_server_submit",
            "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free",
-           "cg_profile_enable", "cg_profile_read", "cg_set_tuning", "cg_get_tuning"]
+           "cg_profile_enable", "cg_profile_read", "cg_set_tuning", "cg_get_tuning", "cg_radius_stats"]
 
 REQ_RADIUS, REQ_KNN = 0, 1
 
@@ -70,6 +70,16 @@ def cg_set_tuning(tuning: dict | None = None):
     for k, v in tuning.items():
         setattr(t, k, v)
     _check(load().cg_set_tuning(ctypes.byref(t)))
+
+
+class RadiusStats(ctypes.Structure):
+    _fields_ = [("tested_pairs", ctypes.c_int64), ("general_groups", ctypes.c_int64), ("groups", ctypes.c_int64)]
+
+
+def cg_radius_stats(h: int) -> dict:
+    s = RadiusStats()
+    _check(load().cg_radius_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in RadiusStats._fields_}
 
 
 def cg_get_tuning() -> dict:
@@ -170,6 +180,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_profile_enable": [I],
             "cg_profile_read": [P, ctypes.c_size_t, P, I],
             "cg_set_tuning": [P],
+            "cg_radius_stats": [P, P],
             "cg_get_tuning": [P],
         }
         for name, args in sig.items():

@@ -630,6 +630,24 @@ cg_status cg_all_points_knn(cg_index_t ix, int32_t k, int32_t* idx_dev, double* 
   return knn_pass(ix, true, nullptr, ix->n, k, idx_dev, d2_dev, (cudaStream_t)stream);
 }
 
+cg_status cg_radius_stats(cg_index_t ix, cg_radius_stats_t* out) {
+  if (!ix || !out) return fail(CG_ERR_INVALID, "NULL argument");
+  memset(out, 0, sizeof *out);
+  const RadiusState& R = ix->ctx.radius;
+  if (!R.valid || R.small || !R.ctrs) return CG_OK;  // no planned count pass on record
+  unsigned long long pairs = 0;
+  uint32_t big = 0;
+  HostRead rd;
+  rd.get(&pairs, R.ctrs + 30, 8);
+  rd.get(&big, R.ctrs + 12, 4);
+  cudaError_t e = rd.sync(ix->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "radius stats");
+  out->tested_pairs = (int64_t)pairs;
+  out->general_groups = big;
+  out->groups = R.all_points && R.zbeg ? (int64_t)R.znb : -1;
+  return CG_OK;
+}
+
 cg_status cg_knn_grow(cg_index_t ix, const double* q_dev, int64_t nq, int32_t k, int32_t policy,
                       int32_t* idx_dev, double* d2_dev, int64_t* visited_dev, void* stream) {
   if (!ix || !idx_dev || (nq > 0 && !q_dev)) return fail(CG_ERR_INVALID, "NULL argument");

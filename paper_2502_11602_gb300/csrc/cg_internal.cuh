@@ -34,7 +34,8 @@ struct Tile {
 // Device status word bits (read by the host after a sync).
 enum : uint32_t {
   ST_NONFINITE = 1u,   // a coordinate was NaN / inf
-  ST_TIMEOUT = 2u,     // a bounded spin gave up
+  ST_TIMEOUT = 2u,     // a bounded spin gave up: the whole pass is void (every
+                       // kernel of it, on every forked stream), the host fails it
   ST_OVERFLOW = 4u,    // an output capacity was exceeded
   ST_INTERNAL = 8u,    // a consistency check failed
   ST_KNN_SLOW = 16u,   // some k-NN queries need the slow path (not an error)

@@ -896,7 +896,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
         return fail(CG_ERR_OOM, "device allocation failed (radius plan)");
       Lbig.qs.blk_list = R.big_list;
       e = launch_radius_plan(ix->precision, kernel, L.iv, L.qs, R.thr, R.plans, R.msize, R.isize, R.big_list,
-                             R.ctrs + 12, C.status, st, zw);
+                             R.ctrs + 12, C.status, st, zw, reinterpret_cast<unsigned long long*>(R.ctrs + 30));
       // 64-bit offsets: a call's mask words may exceed 2^32 (hundreds of
       // millions of queries with wide candidate sets)
       if (e == cudaSuccess) e = exclusive_scan_u32_i64(R.msize, R.moff, nb, sscr, C.status, st);

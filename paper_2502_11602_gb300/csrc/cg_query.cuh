@@ -131,7 +131,8 @@ struct BlockPlan {
 // to the group's height range widened by the kernel's half height and pad.
 cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw = false);
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw = false,
+                               unsigned long long* pairs = nullptr);
 cudaError_t launch_radius_count2(int prec, int kern, const IndexView& iv, const QuerySet& qs,
                                  const Thresholds* thr, const BlockPlan* plans, const int64_t* moff,
                                  const int64_t* idoff, uint32_t* counts, uint32_t* masks, uint32_t* ids,
@@ -182,7 +183,7 @@ inline bool zw_applies(const cg_index* ix, int kern) {
          (kern == CG_SPHERE || kern == CG_CUBE);
 }
 
-// Small query batches (cg_small.cu): one warp per query, no plan.  Calls of
+// Small query batches (cg_small.cu): one block per query, no plan.  Calls of
 // up to kSmallBatch external queries take this path when their rows are at
 // most kSmallRowCap long (checked by the count).
 constexpr int64_t kSmallBatch = 1024;

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
                                                          uint32_t* __restrict__ msize,
                                                          uint32_t* __restrict__ isize,
                                                          uint32_t* __restrict__ big_list, uint32_t* big_n,
-                                                         const uint32_t* status, int zfull, int zw) {
+                                                         const uint32_t* status, int zfull, int zw,
+                                                         unsigned long long* pairs) {
   using R = typename R2<PREC>::T;
   constexpr int KW = R2<PREC>::KW;
   if (replan_pending(status)) return;
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
       msize[b] = big ? 0u : nq * W;
       isize[b] = big ? 0u : K;
       if (big) big_list[atomicAdd(big_n, 1u)] = b;
+      else if (pairs) atomicAdd(pairs, (unsigned long long)K * nq);  // the tests the count kernels run
     }
   }
   // replayed pipelines scan the whole capacity: groups past the true count
@@ -380,14 +382,19 @@ __global__ void __launch_bounds__(CT) radius_count2_kernel(IndexView ix, QuerySe
             : "=r"(done)
             : "r"(mbar), "r"(phase)
             : "memory");
-      if (!done) {
-        atomicOr(status, ST_TIMEOUT);
-        for (uint32_t it = 0; it < kSpinLimit && !done; ++it)  // still bounded
+      if (__syncthreads_or(!done)) {
+        // The pass is void (the host rejects every kernel of it, the other
+        // size classes included, on ST_TIMEOUT): wait once more, still
+        // bounded, for the copies in flight, then stop without computing or
+        // writing anything.
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        for (uint32_t it = 0; it < kSpinLimit && !done; ++it)
           asm volatile(
               "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
               : "=r"(done)
               : "r"(mbar), "r"(phase)
               : "memory");
+        break;
       }
       phase ^= 1u;
     }
@@ -1058,15 +1065,17 @@ int resident_grid(F kern, int threads, size_t smem) {
 
 cudaError_t launch_radius_plan(int prec, int kern, const IndexView& iv, const QuerySet& qs, const Thresholds* thr,
                                BlockPlan* plans, uint32_t* msize, uint32_t* isize, uint32_t* big_list,
-                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw) {
+                               uint32_t* big_n, const uint32_t* status, cudaStream_t st, bool zw,
+                               unsigned long long* pairs) {
   const int zfull = kern == CG_CYLINDER ? 1 : 0;
   const int grid = (int)std::min<int64_t>((qs.nblocks + 3) / 4 + 1, (int64_t)sm_count() * 16);
   ProfScope prof("radius_plan", st);
   if (prec == CG_FP32_OFFSET)
     radius_plan_kernel<1><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull,
-                                               zw ? 1 : 0);
+                                               zw ? 1 : 0, pairs);
   else
-    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull, 0);
+    radius_plan_kernel<0><<<grid, PT, 0, st>>>(iv, qs, thr, plans, msize, isize, big_list, big_n, status, zfull, 0,
+                                               pairs);
   note_launch();
   return cudaGetLastError();
 }

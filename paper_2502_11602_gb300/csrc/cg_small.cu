@@ -1,11 +1,12 @@
-// cg_small.cu -- radius search for small query batches: one warp per query,
+// cg_small.cu -- radius search for small query batches: one block per query,
 // no query plan.
 //
 // The regular path groups the queries by voxel (a sort of the queries, a plan
 // per group, several host reads of sizes) so that a group's candidates are
 // staged once for all of its queries.  For a call of a few hundred queries
-// that set-up costs far more than the search.  Here each warp takes one
-// query and runs Algorithm 1 for it as stated: the voxel range of the
+// that set-up costs far more than the search.  Here a block of SW warps takes
+// one query (its warps split the candidates, so that many loads are in
+// flight) and runs Algorithm 1 for it as stated: the voxel range of the
 // kernel's bounding box (widened by one voxel on each side, so that the
 // rounding of the voxel keys can never hide a point), every point of those
 // voxels tested with the exact binary64 predicate.  A voxel row (2D) or
@@ -14,9 +15,9 @@
 //   count  per query, the number of points inside; then one block scans the
 //          counts into offsets and records the largest row.
 //   fill   per query, the ids of the points inside, gathered in shared
-//          memory, sorted ascending (bitonic) and written out; rows longer
-//          than the shared buffer are refused on the host (the caller then
-//          takes the regular path).
+//          memory, sorted ascending (bitonic, the whole block) and written
+//          out; rows longer than the shared buffer are refused on the host
+//          (the caller then takes the regular path).
 #include <math.h>
 
 #include <algorithm>
@@ -84,19 +85,24 @@ template <int KERN>
 __global__ void __launch_bounds__(SW * 32) small_count_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                               double r, uint32_t* __restrict__ counts,
                                                               uint32_t* status) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t e = blockIdx.x * SW + (threadIdx.x >> 5);
+  __shared__ uint32_t wsum[SW];
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint32_t e = blockIdx.x;
   if (e >= nq) return;
   const double* c = q + 3 * (size_t)e;
   const double r2 = __dmul_rn(r, r);
   uint32_t cnt = 0;
   const bool ok = small_runs<KERN>(ix, c, r, [&](uint32_t t0, uint32_t t1) {
-    for (uint32_t t = t0 + lane; t < t1; t += 32)
+    for (uint32_t t = t0 + threadIdx.x; t < t1; t += SW * 32)
       cnt += exact_in<KERN>(ix.xyz64 + 3 * (size_t)small_id(ix, t), c, r2) ? 1u : 0u;
   });
   cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if (lane == 0) {
-    counts[e] = ok ? cnt : 0u;
+  if (lane == 0) wsum[w] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int i = 0; i < SW; ++i) tot += wsum[i];
+    counts[e] = ok ? tot : 0u;
     if (!ok) atomicOr(status, ST_NONFINITE);
   }
 }
@@ -141,41 +147,37 @@ template <int KERN, int CAP>
 __global__ void __launch_bounds__(SW * 32) small_fill_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                              double r, const int64_t* __restrict__ offsets,
                                                              int32_t* __restrict__ out, uint32_t* status) {
-  __shared__ uint32_t buf[SW][CAP];
-  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const uint32_t e = blockIdx.x * SW + w;
+  __shared__ uint32_t B[CAP];
+  __shared__ uint32_t nhit;
+  const uint32_t e = blockIdx.x;
   if (e >= nq) return;
   const double* c = q + 3 * (size_t)e;
   const double r2 = __dmul_rn(r, r);
-  uint32_t* B = buf[w];
-  uint32_t n = 0;  // hits gathered so far (warp-uniform)
+  if (threadIdx.x == 0) nhit = 0;
+  __syncthreads();
   small_runs<KERN>(ix, c, r, [&](uint32_t t0, uint32_t t1) {
-    for (uint32_t s0 = t0; s0 < t1; s0 += 32) {
-      const uint32_t t = s0 + lane;
-      uint32_t id = 0;
-      bool in = false;
-      if (t < t1) {
-        id = small_id(ix, t);
-        in = exact_in<KERN>(ix.xyz64 + 3 * (size_t)id, c, r2);
+    for (uint32_t t = t0 + threadIdx.x; t < t1; t += SW * 32) {
+      const uint32_t id = small_id(ix, t);
+      if (exact_in<KERN>(ix.xyz64 + 3 * (size_t)id, c, r2)) {
+        const uint32_t at = atomicAdd(&nhit, 1u);
+        if (at < (uint32_t)CAP) B[at] = id;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, in);
-      const uint32_t at = n + (uint32_t)__popc(m & lanemask_lt());
-      if (in && at < (uint32_t)CAP) B[at] = id;
-      n += (uint32_t)__popc(m);
     }
   });
+  __syncthreads();
+  const uint32_t n = nhit;
   const int64_t o0 = offsets[e];
   if ((int64_t)n != offsets[e + 1] - o0 || n > (uint32_t)CAP) {  // count and fill disagree, or too long
-    if (lane == 0) atomicOr(status, ST_INTERNAL);
+    if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
   uint32_t n2 = 1;
   while (n2 < n) n2 <<= 1;
-  for (uint32_t i = n + lane; i < n2; i += 32) B[i] = 0xffffffffu;
-  __syncwarp();
+  for (uint32_t i = n + threadIdx.x; i < n2; i += SW * 32) B[i] = 0xffffffffu;
+  __syncthreads();
   for (uint32_t k = 2; k <= n2; k <<= 1)  // bitonic sort of the row, ascending
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = lane; i < n2; i += 32) {
+      for (uint32_t i = threadIdx.x; i < n2; i += SW * 32) {
         const uint32_t l = i ^ j;
         if (l > i) {
           const uint32_t a = B[i], b = B[l];
@@ -185,9 +187,9 @@ __global__ void __launch_bounds__(SW * 32) small_fill_kernel(IndexView ix, const
           }
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
-  for (uint32_t i = lane; i < n; i += 32) out[o0 + i] = (int32_t)B[i];
+  for (uint32_t i = threadIdx.x; i < n; i += SW * 32) out[o0 + i] = (int32_t)B[i];
 }
 
 }  // namespace
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(SW * 32) small_fill_kernel(IndexView ix, const
 cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
                                uint32_t* counts, int64_t* offsets, uint32_t* stats, uint32_t* status,
                                cudaStream_t st) {
-  const int grid = (int)((nq + SW - 1) / SW);
+  const int grid = (int)nq;  // a block per query
   ProfScope prof("radius_small_count", st);
   if (kern == CG_SPHERE) small_count_kernel<CG_SPHERE><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, status);
   else if (kern == CG_CUBE) small_count_kernel<CG_CUBE><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, status);
@@ -210,7 +212,7 @@ cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, u
 
 cudaError_t launch_small_fill(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
                               const int64_t* offsets, int32_t* out, uint32_t* status, cudaStream_t st) {
-  const int grid = (int)((nq + SW - 1) / SW);
+  const int grid = (int)nq;  // a block per query
   ProfScope prof("radius_small_fill", st);
   if (kern == CG_SPHERE)
     small_fill_kernel<CG_SPHERE, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, offsets, out, status);

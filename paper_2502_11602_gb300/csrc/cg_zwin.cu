@@ -62,8 +62,19 @@ __device__ __forceinline__ void bitonic_u64(unsigned long long* K, uint32_t n2, 
     }
 }
 
+// One compare-exchange step of a bitonic network held in registers: element
+// e of the network, partner e ^ j (a lane of the same register), block size k.
+__device__ __forceinline__ unsigned long long bitonic_step(unsigned long long key, uint32_t e, uint32_t j,
+                                                           uint32_t k) {
+  const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, (int)j);
+  const bool keep_min = ((e & j) == 0) == ((e & k) == 0);
+  return keep_min ? (o < key ? o : key) : (o > key ? o : key);
+}
+
 // Runs of up to ZS_SHORT points: one warp each, sorted by (height, position
-// in the id-ordered run); longer runs are listed for zsort_long_kernel.
+// in the id-ordered run): up to 64 points in registers (two per lane),
+// longer in shared memory; runs longer than ZS_SHORT are listed for
+// zsort_long_kernel.
 __global__ void __launch_bounds__(ZS_WARPS * 32) zsort_short_kernel(const float4* __restrict__ in,
                                                                     float4* __restrict__ out,
                                                                     uint32_t* __restrict__ sid_out,
@@ -88,6 +99,36 @@ __global__ void __launch_bounds__(ZS_WARPS * 32) zsort_short_kernel(const float4
       if (lane == 0 && len == 1) {
         out[s] = in[s];
         sid_out[s] = __float_as_uint(in[s].w);
+      }
+      continue;
+    }
+    if (len <= 64) {
+      // elements lane and lane + 32; padding keys sort last
+      unsigned long long k0 = lane < len ? ((unsigned long long)z_order_key(in[s + lane].z) << 32) | lane : ~0ull;
+      unsigned long long k1 =
+          lane + 32 < len ? ((unsigned long long)z_order_key(in[s + lane + 32].z) << 32) | (lane + 32) : ~0ull;
+      const uint32_t n2 = len <= 32 ? 32u : 64u;
+      for (uint32_t k = 2; k <= n2; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          if (j == 32) {  // elements lane and lane + 32: in one lane
+            const bool up = (lane & k) == 0;
+            const unsigned long long lo = k0 < k1 ? k0 : k1, hi = k0 < k1 ? k1 : k0;
+            k0 = up ? lo : hi;
+            k1 = up ? hi : lo;
+          } else {
+            k0 = bitonic_step(k0, lane, j, k);
+            if (n2 == 64) k1 = bitonic_step(k1, lane + 32, j, k);
+          }
+        }
+      if (lane < len) {
+        const float4 rec = in[s + (uint32_t)k0];
+        out[s + lane] = rec;
+        sid_out[s + lane] = __float_as_uint(rec.w);
+      }
+      if (lane + 32 < len) {
+        const float4 rec = in[s + (uint32_t)k1];
+        out[s + lane + 32] = rec;
+        sid_out[s + lane + 32] = __float_as_uint(rec.w);
       }
       continue;
     }

@@ -82,6 +82,12 @@ def test_tuned_launch_shapes_pipeline_matches_oracle(tmp_path):
     assert tuning["count_shape"] in autotune.SHAPES and tuning["fill_shape"] in autotune.SHAPES
     tuning2, report2 = autotune.tune_launch(xyz, off, cells, radius=1.0, cache_path=path)
     assert report2 == {} and tuning2 == tuning
+    # launch shapes of a captured batch, timed on the batch
+    x = torch.from_numpy(xyz).to("cuda:0")
+    shapes, prep = autotune.tune_pipeline(x, off, cells, radius=1.0, k=0, cache_path=path)
+    assert set(shapes) == {"count_shape", "fill_shape"} and len(prep) >= 5
+    assert autotune.tune_pipeline(x, off, cells, radius=1.0, k=0, cache_path=path) == (shapes, {})
+    tuning = dict(tuning, **shapes)
     saved = cg.cg_get_tuning()
     cg.cg_set_tuning(tuning)
     try:

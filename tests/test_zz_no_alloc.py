@@ -71,3 +71,36 @@ def test_noalloc_scan_repeat_same_input_and_limits():
     dummy = torch.zeros(2, dtype=torch.int64, device=DEV)
     assert _scan_noalloc(dummy, big, dummy) == 1
     assert b"max 134217728" in cg.load().cg_last_error()
+
+
+def test_noalloc_scan_misaligned_counts():
+    # counts that start 4 bytes past a 16-byte boundary take the scalar loads
+    base = torch.randint(0, 1 << 20, (10_001,), dtype=torch.int32, device=DEV)
+    c = base[1:]
+    n = 10_000
+    out = torch.full((n + 1,), -5, dtype=torch.int64, device=DEV)
+    assert _scan_noalloc(c, n, out) == 0
+    torch.cuda.synchronize()
+    expect = np.zeros(n + 1, np.int64)
+    np.cumsum(c.cpu().numpy().astype(np.int64), out=expect[1:])
+    assert np.array_equal(out.cpu().numpy(), expect)
+
+
+def test_noalloc_scan_at_the_documented_maximum():
+    # n = 2^27: all 65536 tiles of the fixed scratch, the last status word
+    # included; totals well above 2^32 exercise the 62-bit packed prefixes
+    n = 134_217_728
+    g = torch.Generator(device=DEV).manual_seed(7)
+    c = torch.randint(0, 1 << 7, (n,), dtype=torch.int32, device=DEV, generator=g)
+    out = torch.full((n + 1,), -9, dtype=torch.int64, device=DEV)
+    assert _scan_noalloc(c, n, out) == 0, cg.load().cg_last_error()
+    torch.cuda.synchronize()
+    host = c.cpu().numpy().astype(np.int64)
+    expect = np.zeros(n + 1, np.int64)
+    np.cumsum(host, out=expect[1:])
+    assert expect[-1] > (1 << 32)
+    got = out.cpu().numpy()
+    assert got[-1] == expect[-1]
+    assert np.array_equal(got, expect)
+    del c, out
+    torch.cuda.empty_cache()
