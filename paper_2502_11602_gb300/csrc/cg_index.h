@@ -83,6 +83,12 @@ struct RadiusState {
   uint32_t *zbeg = nullptr, *zkey = nullptr;
   uint32_t znb = 0;
   bool small = false;  // the count took the small-batch path (so does the fill)
+  // the small-batch path's workspace, allocated once for kSmallBatch queries
+  // and kept until the context is released: counts, sizes, sorted rows
+  // (kSmallRowCap entries per query)
+  DevBufs small_bufs;
+  uint32_t *small_counts = nullptr, *small_stats = nullptr;
+  int32_t* small_rows = nullptr;
 };
 
 // Mutable state of queries against an index: the external query plan, the
@@ -96,6 +102,7 @@ struct QueryCtx {
   void release(cudaStream_t st) {
     plan.bufs.release(st);
     radius.bufs.release(st);
+    radius.small_bufs.release(st);
     plan = QueryPlan();
     radius = RadiusState();
   }
@@ -214,9 +221,11 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
 cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
                    double* d2, cudaStream_t st);
 // Algorithm 2 step by step under a growth policy (0 monotone, 1 density),
-// with the voxels each search visited (cg_knn.cu).
+// with the voxels each search visited (cg_knn.cu); with a list, only the
+// queries it names (its length on the device).
 cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
-                        int64_t* visited, cudaStream_t st, uint32_t* status = nullptr);
+                        int64_t* visited, cudaStream_t st, uint32_t* status = nullptr,
+                        const uint32_t* list = nullptr, const uint32_t* list_n = nullptr);
 cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
 cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
 cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,

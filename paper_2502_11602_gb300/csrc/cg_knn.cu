@@ -67,6 +67,13 @@ __device__ __forceinline__ double exact_d2(const double* __restrict__ p, const d
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Squared distances are non-negative binary64 values or +inf: their bit
+// patterns order as unsigned integers, so the comparisons, minima and maxima
+// of the (d2, id) order run on the integer pipes (the binary64 pipe of a
+// GB300 is about 1/64 of the binary32 rate and is kept for the distances).
+__device__ __forceinline__ unsigned long long dbits(double d) { return (unsigned long long)__double_as_longlong(d); }
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+
 // Bound on |d2f - d2| for candidates with d2 about tau (the model of the
 // radius thresholds, two-sided, doubled).  Zero for binary64 records.
 struct KBound {
@@ -131,7 +138,8 @@ __device__ void warp_sort_list(double* d2, uint32_t* id, int P) {
         bool asc = (lo & k) == 0;
         double a = d2[lo], b = d2[hi];
         uint32_t ia = id[lo], ib = id[hi];
-        bool gt = (a > b) || (a == b && ia > ib);
+        const unsigned long long ka = dbits(a), kb = dbits(b);
+        bool gt = ka > kb || (ka == kb && ia > ib);
         if (gt == asc) { d2[lo] = b; d2[hi] = a; id[lo] = ib; id[hi] = ia; }
       }
       __syncwarp();
@@ -634,7 +642,8 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
           bool sw = false;
 #pragma unroll
           for (int i = 0; i + 1 < L; ++i) {
-            const bool gt = ex[i] > ex[i + 1] || (ex[i] == ex[i + 1] && cid[i] > cid[i + 1]);
+            const unsigned long long ka = dbits(ex[i]), kb = dbits(ex[i + 1]);
+            const bool gt = ka > kb || (ka == kb && cid[i] > cid[i + 1]);
             if (gt) {
               const double te = ex[i]; ex[i] = ex[i + 1]; ex[i + 1] = te;
               const uint32_t tc = cid[i]; cid[i] = cid[i + 1]; cid[i + 1] = tc;
@@ -643,12 +652,14 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
           }
           if (!sw) break;
         }
+        unsigned long long kbits = 0;
 #pragma unroll
-        for (int i = 0; i < L; ++i) kth = fmax(kth, i < kk ? ex[i] : 0.0);  // ex ascending
+        for (int i = 0; i < L; ++i) kbits = max(kbits, i < kk ? dbits(ex[i]) : 0ull);  // ex ascending
+        kth = __longlong_as_double((long long)kbits);
         undecided = !exhausted && !(kth < (double)W2);
       }
       if (undecided) {
-        if (found >= k && kk > 0 && kth < INFINITY) {
+        if (found >= k && kk > 0 && dbits(kth) < kInfBits) {
           // the k-th value inside the box bounds the true k-th from above:
           // the bounded search covers that sphere
           const uint32_t e = atomicAdd(bcnt, 1u);
@@ -695,11 +706,17 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
                                                                      uint32_t* __restrict__ slow_list,
                                                                      uint32_t* slow_cnt, const uint32_t* status) {
   if (replan_pending(status)) return;
-  __shared__ double s_d2[KB_WARPS][KB_CAP];
+  // per warp: the candidates' ids and binary32 values, then the band's ids
+  // and exact values (at most KB_CAP / 2 of them)
+  __shared__ double s_d2[KB_WARPS][KB_CAP / 2];
+  __shared__ float s_f[KB_WARPS][KB_CAP];
   __shared__ uint32_t s_id[KB_WARPS][KB_CAP];
+  __shared__ uint32_t s_bid[KB_WARPS][KB_CAP / 2];
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   double* wd2 = s_d2[warp];
+  float* wf = s_f[warp];
   uint32_t* wid = s_id[warp];
+  uint32_t* bid = s_bid[warp];
   const Thresholds thr = *thr_p;
   const KBound kb = make_kbound<1>(thr);
   const float4* __restrict__ pts = ix.pts32;
@@ -760,10 +777,14 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float dx = __fsub_rn(p[u].x, q.x), dy = __fsub_rn(p[u].y, q.y), dz = __fsub_rn(p[u].z, q.z);
-          pick[u] = pick[u] && __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) <= cut;
+          const float dv = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          pick[u] = pick[u] && dv <= cut;
           const unsigned bm = __ballot_sync(0xffffffffu, pick[u]);
           const uint32_t pos = m + __popc(bm & lanemask_lt());
-          if (pick[u] && pos < (uint32_t)KB_CAP) wid[pos] = __float_as_uint(p[u].w);
+          if (pick[u] && pos < (uint32_t)KB_CAP) {
+            wid[pos] = __float_as_uint(p[u].w);
+            wf[pos] = dv;
+          }
           m += __popc(bm);
         }
       }
@@ -774,16 +795,48 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
       continue;
     }
     __syncwarp();
-    int P = 32;
-    while (P < (int)m) P <<= 1;
-    for (int i = (int)lane; i < P; i += 32) {
-      if (i < (int)m) wd2[i] = exact_d2(ix.xyz64 + 3 * (size_t)wid[i], q64 + 3 * (size_t)qid);
-      else { wd2[i] = INFINITY; wid[i] = 0xffffffffu; }
+    // the k-th smallest binary32 value tau (bisection on the bit patterns of
+    // the non-negative values), then the band d2f <= tau + 2 B(tau): it
+    // holds every point of the true k nearest (there are k candidates with
+    // d2f <= tau, so the exact k-th is at most tau + B(tau))
+    uint32_t klo = 0u, khi = 0x7f800000u;
+    while (klo < khi) {
+      const uint32_t mid = klo + ((khi - klo) >> 1);
+      uint32_t c = 0;
+      for (uint32_t i = lane; i < m; i += 32) c += __float_as_uint(wf[i]) <= mid ? 1u : 0u;
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (c >= (uint32_t)k) khi = mid;
+      else klo = mid + 1u;
+    }
+    const float tau = __uint_as_float(klo);
+    const float bcut = __fadd_ru(tau, 2.0f * kb.at(tau));
+    // the band, compacted to the front of the exact list (slots [0, mb))
+    uint32_t mb = 0;
+    for (uint32_t i0 = 0; i0 < m; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool in = i < m && wf[i] <= bcut;
+      const uint32_t cid = in ? wid[i] : 0u;
+      const unsigned bm = __ballot_sync(0xffffffffu, in);
+      const uint32_t pos = mb + __popc(bm & lanemask_lt());
+      if (in && pos < (uint32_t)(KB_CAP / 2)) bid[pos] = cid;
+      mb += __popc(bm);
+    }
+    if (mb > (uint32_t)(KB_CAP / 2)) {  // a band this wide (ties): the ring path
+      if (lane == 0) slow_list[atomicAdd(slow_cnt, 1u)] = qid;
+      __syncwarp();
+      continue;
     }
     __syncwarp();
-    warp_sort_list(wd2, wid, P);
+    int P = 32;
+    while (P < (int)mb) P <<= 1;
+    for (int i = (int)lane; i < P; i += 32) {
+      if (i < (int)mb) wd2[i] = exact_d2(ix.xyz64 + 3 * (size_t)bid[i], q64 + 3 * (size_t)qid);
+      else { wd2[i] = INFINITY; bid[i] = 0xffffffffu; }
+    }
+    __syncwarp();
+    warp_sort_list(wd2, bid, P);
     for (int i = (int)lane; i < k; i += 32) {
-      out_idx[(size_t)qid * k + i] = (int32_t)wid[i];
+      out_idx[(size_t)qid * k + i] = (int32_t)bid[i];
       if (out_d2) out_d2[(size_t)qid * k + i] = wd2[i];
     }
     __syncwarp();
@@ -800,7 +853,8 @@ struct WarpList {
 };
 
 __device__ __forceinline__ bool lt(double a, uint32_t ia, double b, uint32_t ib) {
-  return a < b || (a == b && ia < ib);
+  const unsigned long long ka = dbits(a), kb = dbits(b);
+  return ka < kb || (ka == kb && ia < ib);
 }
 
 __device__ void wl_insert(WarpList& L, double d, uint32_t id, int cap) {
@@ -826,6 +880,8 @@ __device__ __forceinline__ double wl_get(const WarpList& L, int slot) {
   return slot < 32 ? a : b;
 }
 
+__device__ void knn_thresholds(Thresholds* out, double e_p, double e_q);
+
 template <int PREC>
 __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs, int k,
                                                        const uint32_t* __restrict__ slow_list,
@@ -839,12 +895,43 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
     const uint32_t qid = slow_list[e];
     const double* c = q64 + 3 * (size_t)qid;
     const Tile& T = ix.tiles[(qs.all_points && ix.ntiles > 1) ? tile_of_id(ix.tiles, ix.ntiles, qid) : 0];
-    // the query's voxel (clamped), from binary64
+    // the query's voxel (clamped), from binary64 on lane 0 (the binary64
+    // pipe is narrow), then broadcast
     int cc[3] = {0, 0, 0};
-    for (int a = 0; a < ix.dim; ++a) {
-      double v = floor(__ddiv_rn(__dsub_rn(__ldg(c + a), T.lo[a]), T.s[a]));
-      v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
-      cc[a] = (int)v;
+    if (lane == 0)
+      for (int a = 0; a < ix.dim; ++a) {
+        double v = floor(__ddiv_rn(__dsub_rn(__ldg(c + a), T.lo[a]), T.s[a]));
+        v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
+        cc[a] = (int)v;
+      }
+    for (int a = 0; a < 3; ++a) cc[a] = __shfl_sync(0xffffffffu, cc[a], 0);
+    // the query's record in the tile's frame and the screen's error bound
+    using R = typename KRec<PREC>::T;
+    const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32) : reinterpret_cast<const R*>(ix.pts64s);
+    R qr;
+    KBound kb;
+    if constexpr (PREC == 1) {
+      float4 qf = make_float4(0.f, 0.f, 0.f, 0.f);
+      KBound k0 = {0.f, 0.f, 0.f};
+      if (lane == 0) {  // binary64 on one lane
+        qf.x = __double2float_rn(__dsub_rn(__ldg(c), T.origin[0]));
+        qf.y = __double2float_rn(__dsub_rn(__ldg(c + 1), T.origin[1]));
+        qf.z = __double2float_rn(__dsub_rn(__ldg(c + 2), T.origin[2]));
+        const double m = (double)fmaxf(fabsf(qf.x), fmaxf(fabsf(qf.y), fabsf(qf.z)));
+        Thresholds th;
+        knn_thresholds(&th, (double)T.enc_err, ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30);
+        k0 = make_kbound<1>(th);
+      }
+      qr = make_float4(__shfl_sync(0xffffffffu, qf.x, 0), __shfl_sync(0xffffffffu, qf.y, 0),
+                       __shfl_sync(0xffffffffu, qf.z, 0), 0.f);
+      kb.c1 = __shfl_sync(0xffffffffu, k0.c1, 0);
+      kb.c0 = __shfl_sync(0xffffffffu, k0.c0, 0);
+      kb.c2 = __shfl_sync(0xffffffffu, k0.c2, 0);
+    } else {
+      qr = make_double4_32a(__ldg(c), __ldg(c + 1), __ldg(c + 2), 0.0);
+      Thresholds th;
+      th.pad_[0] = 0.f;
+      kb = make_kbound<0>(th);
     }
     WarpList L;
     L.d[0] = L.d[1] = INFINITY;
@@ -880,12 +967,17 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
             uint32_t t = t0 + lane;
             double d = INFINITY;
             uint32_t id = 0xffffffffu;
-            if (t < sp.y) {
-              id = PREC == 1 ? __float_as_uint(ix.pts32[t].w) : (uint32_t)__double_as_longlong(ix.pts64s[t].w);
-              d = exact_d2(ix.xyz64 + 3 * (size_t)id, c);
-            }
             const double worst = wl_get(L, k - 1);
             const uint32_t worst_id = __shfl_sync(0xffffffffu, (k - 1) < 32 ? L.id[0] : L.id[1], (k - 1) & 31);
+            const float wf = __double2float_ru(worst);
+            if (t < sp.y) {
+              // the binary32 screen: a candidate whose value, less its error
+              // bound, exceeds the current k-th cannot enter the list
+              const R rec = pts[t];
+              id = krec_id(rec);
+              const float df = kd2f(rec, qr);
+              if (!(__fsub_rd(df, kb.at(df)) > wf)) d = exact_d2(ix.xyz64 + 3 * (size_t)id, c);
+            }
             unsigned cand = __ballot_sync(0xffffffffu, t < sp.y && lt(d, id, worst, worst_id));
             while (cand) {
               int src = __ffs(cand) - 1;
@@ -901,17 +993,21 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
       if (covers) break;
       // stop when the k-th is strictly inside the visited box (binary64 wall)
       const double kth = wl_get(L, k - 1);
-      if (kth < INFINITY) {
-        double w = INFINITY;
-        for (int a = 0; a < ix.dim; ++a) {
-          double x = __ldg(c + a);
-          if (lo[a] > 0) w = fmin(w, x - (T.lo[a] + (double)lo[a] * T.s[a]));
-          if (hi[a] < T.n[a] - 1) w = fmin(w, (T.lo[a] + (double)(hi[a] + 1) * T.s[a]) - x);
+      if (dbits(kth) < kInfBits) {
+        int stop = 0;
+        if (lane == 0) {  // binary64 on one lane, then broadcast
+          double w = INFINITY;
+          for (int a = 0; a < ix.dim; ++a) {
+            double x = __ldg(c + a);
+            if (lo[a] > 0) w = fmin(w, x - (T.lo[a] + (double)lo[a] * T.s[a]));
+            if (hi[a] < T.n[a] - 1) w = fmin(w, (T.lo[a] + (double)(hi[a] + 1) * T.s[a]) - x);
+          }
+          // margin for the rounding of the voxel keys and of the wall itself
+          double slack = 1e-12 * (fabs(T.lo[0]) + fabs(T.lo[1]) + fabs(T.lo[2]) + 1.0);
+          w -= slack;
+          stop = (w > 0 && kth < w * w * (1.0 - 1e-12)) ? 1 : 0;
         }
-        // margin for the rounding of the voxel keys and of the wall itself
-        double slack = 1e-12 * (fabs(T.lo[0]) + fabs(T.lo[1]) + fabs(T.lo[2]) + 1.0);
-        w -= slack;
-        if (w > 0 && kth < w * w * (1.0 - 1e-12)) break;
+        if (__shfl_sync(0xffffffffu, stop, 0)) break;
       }
     }
     // write out: slot s lives in lane s % 32, register s / 32
@@ -919,7 +1015,7 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
       double d = wl_get(L, s);
       uint32_t id = __shfl_sync(0xffffffffu, s < 32 ? L.id[0] : L.id[1], s & 31);
       if (lane == 0) {
-        bool ok = d < INFINITY;
+        bool ok = dbits(d) < kInfBits;
         out_idx[(size_t)qid * k + s] = ok ? (int32_t)id : -1;
         if (out_d2) out_d2[(size_t)qid * k + s] = ok ? d : INFINITY;
       }
@@ -943,15 +1039,19 @@ template <int PREC>
 __global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                        int k, int policy, int32_t* __restrict__ out_idx,
                                                        double* __restrict__ out_d2,
-                                                       long long* __restrict__ visited, uint32_t* status) {
+                                                       long long* __restrict__ visited, uint32_t* status,
+                                                       const uint32_t* __restrict__ list, const uint32_t* list_n) {
   const unsigned lane = threadIdx.x & 31u;
   const Tile& T = ix.tiles[0];
   const int nax = ix.dim;
   double smin = fmin(T.s[0], T.s[1]);
   if (nax == 3) smin = fmin(smin, T.s[2]);
   const double kPi = 3.14159265358979323846;
-  for (uint32_t e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); e < nq;
-       e += gridDim.x * (blockDim.x / 32)) {
+  // every query, or the queries of a list (those another kernel left)
+  const uint32_t nrun = list ? min(*list_n, nq) : nq;
+  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nrun;
+       w += gridDim.x * (blockDim.x / 32)) {
+    const uint32_t e = list ? list[w] : w;
     const double* c = q + 3 * (size_t)e;
     const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
     WarpList L;
@@ -1049,7 +1149,7 @@ __global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const doubl
       const double d = wl_get(L, s);
       const uint32_t id = __shfl_sync(0xffffffffu, s < 32 ? L.id[0] : L.id[1], s & 31);
       if (lane == 0) {
-        const bool ok = d < INFINITY;
+        const bool ok = dbits(d) < kInfBits;
         out_idx[(size_t)e * k + s] = ok ? (int32_t)id : -1;
         if (out_d2) out_d2[(size_t)e * k + s] = ok ? d : INFINITY;
       }
@@ -1085,6 +1185,247 @@ __global__ void knn_thr_tiles_kernel(Thresholds* out, const Tile* __restrict__ t
   for (int t = threadIdx.x; t < ntiles; t += 32) e = fmaxf(e, tiles[t].enc_err);
   for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
   if (threadIdx.x == 0) knn_thresholds(out, (double)e, (double)e);
+}
+
+// ---------------------------------------------------------------- small batches
+
+// Small batches of external queries (at most kSmallBatch): one block of
+// KS_T threads per query, no query plan.  Boxes of R = 1, 2, ... voxel rings
+// around the query's voxel are gathered until they hold k points (every
+// candidate: one record load, its binary32 screen value); the k-th smallest
+// screen value tau (bisection on the bit patterns) gives the band
+// d2f <= tau + 2 B(tau), which holds the box's k nearest; their binary64
+// values sorted by (d2, id) give the box's k-th value kth.  If kth is below
+// the squared distance to the box's walls the answer is final; else the
+// true k nearest all lie within sqrt(kth) (the box already holds k points
+// that close), and the voxel range of Algorithm 1 for that radius is
+// gathered and searched once more (final).  A box of more than KS_CAP
+// points or a band wider than KS_BAND sends the query to the step-by-step
+// kernel (the overflow list).
+constexpr int KS_T = kBoxThreads;
+constexpr int KS_CAP = 4096;
+constexpr int KS_BAND = 256;
+constexpr int KS_MAX_RING = 64;
+
+template <int PREC>
+__global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
+                                                         int k, int32_t* __restrict__ out_idx,
+                                                         double* __restrict__ out_d2, uint32_t* __restrict__ over_list,
+                                                         uint32_t* over_n, uint32_t* status) {
+  using R = typename KRec<PREC>::T;
+  __shared__ float s_f[KS_CAP];
+  __shared__ uint32_t s_id[KS_CAP];
+  __shared__ double s_d[KS_BAND];
+  __shared__ uint32_t s_bid[KS_BAND];
+  __shared__ uint32_t s_red[KS_T / 32];
+  __shared__ uint32_t s_start[kBoxThreads + 1], s_off[kBoxThreads + 1];
+  __shared__ uint32_t s_n, s_mb;
+  __shared__ int s_box[8];  // lo[3], hi[3], covers, final
+  __shared__ R s_q;
+  __shared__ KBound s_kb;
+  const uint32_t e = blockIdx.x;
+  if (e >= nq) return;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const Tile& T = ix.tiles[0];
+  const int nax = ix.dim;
+  const double* c = q + 3 * (size_t)e;
+  const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
+  int32_t* oi = out_idx + (size_t)e * k;
+  double* od = out_d2 ? out_d2 + (size_t)e * k : nullptr;
+  if (!(isfinite(cx[0]) && isfinite(cx[1]) && isfinite(cx[2]))) {
+    if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+    for (int i = (int)threadIdx.x; i < k; i += KS_T) {
+      oi[i] = -1;
+      if (od) od[i] = INFINITY;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    if constexpr (PREC == 1) {
+      const float x = __double2float_rn(__dsub_rn(cx[0], T.origin[0]));
+      const float y = __double2float_rn(__dsub_rn(cx[1], T.origin[1]));
+      const float z = __double2float_rn(__dsub_rn(cx[2], T.origin[2]));
+      s_q = make_float4(x, y, z, 0.f);
+      const double m = (double)fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+      Thresholds th;
+      knn_thresholds(&th, (double)T.enc_err, ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30);
+      s_kb = make_kbound<1>(th);
+    } else {
+      s_q = make_double4_32a(cx[0], cx[1], cx[2], 0.0);
+      Thresholds th;
+      knn_thresholds(&th, 0.0, 0.0);
+      s_kb = make_kbound<0>(th);
+    }
+  }
+  // the query's voxel (clamped); binary64 arithmetic runs on thread 0 only
+  // (the binary64 pipe is narrow: a division by all 256 threads costs more
+  // than the whole gather)
+  int cc[3] = {0, 0, 0};
+  if (threadIdx.x == 0)
+    for (int a = 0; a < nax; ++a) {
+      double v = floor(__ddiv_rn(__dsub_rn(cx[a], T.lo[a]), T.s[a]));
+      v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
+      cc[a] = (int)v;
+    }
+  __syncthreads();
+  const R qr = s_q;
+  const KBound kb = s_kb;
+  const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32) : reinterpret_cast<const R*>(ix.pts64s);
+  // block-wide sum of one value per thread (every thread gets it)
+  auto block_sum = [&](uint32_t v) -> uint32_t {
+    v = __reduce_add_sync(0xffffffffu, v);
+    __syncthreads();
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < KS_T / 32; ++w) t += s_red[w];
+    return t;
+  };
+  int Rr = 1;
+  bool final_box = false;
+  uint32_t mb = 0;
+  for (;;) {
+    // the box (thread 0): rings around the query's voxel, or the final
+    // ball's range
+    if (threadIdx.x == 0) {
+      const double rb = final_box ? sqrt(s_d[k - 1]) : 0.0;
+      int cov = 1;
+      for (int a = 0; a < 3; ++a) {
+        int l0, h0;
+        if (a >= nax) {
+          l0 = 0;
+          h0 = T.n[a] - 1;
+        } else if (!final_box) {
+          l0 = max(cc[a] - Rr, 0);
+          h0 = min(cc[a] + Rr, T.n[a] - 1);
+        } else {
+          const double l = floor(__ddiv_rn(__dsub_rn(__dsub_rn(cx[a], rb), T.lo[a]), T.s[a])) - 1.0;
+          const double h = floor(__ddiv_rn(__dsub_rn(__dadd_rn(cx[a], rb), T.lo[a]), T.s[a])) + 1.0;
+          l0 = l < 0.0 ? 0 : (l > (double)(T.n[a] - 1) ? T.n[a] - 1 : (int)l);
+          h0 = h < 0.0 ? 0 : (h > (double)(T.n[a] - 1) ? T.n[a] - 1 : (int)h);
+        }
+        if (a < nax) cov &= (l0 == 0 && h0 == T.n[a] - 1) ? 1 : 0;
+        s_box[a] = l0;
+        s_box[3 + a] = h0;
+      }
+      s_box[6] = cov;
+      s_n = 0;
+    }
+    __syncthreads();  // also: every thread has read s_d before the band is rebuilt
+    const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
+    const bool covers = s_box[6] != 0;
+    // gather: every point of the box, its screen value and id
+    for_each_in_box(ix, T, lo, hi, s_start, s_off, [&](uint32_t t, bool valid) {
+      float df = 0.f;
+      uint32_t id = 0;
+      if (valid) {
+        const R rec = pts[t];
+        df = kd2f(rec, qr);
+        id = krec_id(rec);
+      }
+      const unsigned bm = __ballot_sync(0xffffffffu, valid);
+      uint32_t base = 0;
+      if (lane == 0 && bm) base = atomicAdd(&s_n, (uint32_t)__popc(bm));
+      const uint32_t pos = __shfl_sync(0xffffffffu, base, 0) + __popc(bm & lanemask_lt());
+      if (valid && pos < (uint32_t)KS_CAP) {
+        s_f[pos] = df;
+        s_id[pos] = id;
+      }
+    });
+    __syncthreads();
+    const uint32_t n = s_n;
+    if (n > (uint32_t)KS_CAP) break;  // too many points: the step-by-step kernel
+    if (n < (uint32_t)k && !covers && !final_box) {
+      if (++Rr > KS_MAX_RING) break;
+      continue;
+    }
+    // the k-th smallest screen value (every value when fewer than k)
+    const uint32_t kk = min((uint32_t)k, n);
+    uint32_t klo = 0u, khi = 0x7f800000u;
+    while (kk > 0 && klo < khi) {
+      const uint32_t mid = klo + ((khi - klo) >> 1);
+      uint32_t cnt = 0;
+      for (uint32_t i = threadIdx.x; i < n; i += KS_T) cnt += __float_as_uint(s_f[i]) <= mid ? 1u : 0u;
+      if (block_sum(cnt) >= kk) khi = mid;
+      else klo = mid + 1u;
+    }
+    const float tau = __uint_as_float(klo);
+    const float bcut = kk < (uint32_t)k ? INFINITY : __fadd_ru(tau, 2.0f * kb.at(tau));
+    if (threadIdx.x == 0) s_mb = 0;
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 < n; i0 += KS_T) {
+      const uint32_t i = i0 + threadIdx.x;
+      const bool in = i < n && s_f[i] <= bcut;
+      const unsigned bm = __ballot_sync(0xffffffffu, in);
+      uint32_t base = 0;
+      if (lane == 0 && bm) base = atomicAdd(&s_mb, (uint32_t)__popc(bm));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const uint32_t pos = base + __popc(bm & lanemask_lt());
+      if (in && pos < (uint32_t)KS_BAND) s_bid[pos] = s_id[i];
+    }
+    __syncthreads();
+    mb = s_mb;
+    if (mb > (uint32_t)KS_BAND) break;  // a band this wide (ties): the step-by-step kernel
+    uint32_t P = 1;
+    while (P < mb) P <<= 1;
+    for (uint32_t i = threadIdx.x; i < P; i += KS_T) {
+      if (i < mb) s_d[i] = exact_d2(ix.xyz64 + 3 * (size_t)s_bid[i], c);
+      else { s_d[i] = INFINITY; s_bid[i] = 0xffffffffu; }
+    }
+    __syncthreads();
+    for (uint32_t kq = 2; kq <= P; kq <<= 1)  // bitonic sort by (d2, id)
+      for (uint32_t j = kq >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < P; i += KS_T) {
+          const uint32_t l = i ^ j;
+          if (l > i) {
+            const unsigned long long ka = dbits(s_d[i]), kv = dbits(s_d[l]);
+            const uint32_t ia = s_bid[i], il = s_bid[l];
+            const bool gt = ka > kv || (ka == kv && ia > il);
+            if (gt == ((i & kq) == 0)) {
+              const double td = s_d[i];
+              s_d[i] = s_d[l];
+              s_d[l] = td;
+              s_bid[i] = il;
+              s_bid[l] = ia;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (final_box || covers || kk < (uint32_t)k) {
+      mb = min(mb, (uint32_t)k);
+      goto out;
+    }
+    {
+      // final when the k-th value lies strictly inside the box's walls
+      if (threadIdx.x == 0) {
+        const double kth = s_d[k - 1];
+        double w = INFINITY;
+        for (int a = 0; a < nax; ++a) {
+          if (lo[a] > 0) w = fmin(w, cx[a] - (T.lo[a] + (double)lo[a] * T.s[a]));
+          if (hi[a] < T.n[a] - 1) w = fmin(w, (T.lo[a] + (double)(hi[a] + 1) * T.s[a]) - cx[a]);
+        }
+        w -= 1e-12 * (fabs(T.lo[0]) + fabs(T.lo[1]) + fabs(T.lo[2]) + 1.0);
+        s_box[7] = (w > 0 && kth < w * w * (1.0 - 1e-12)) ? 1 : 0;
+      }
+      __syncthreads();
+      if (s_box[7]) {
+        mb = (uint32_t)k;
+        goto out;
+      }
+    }
+    final_box = true;
+  }
+  // not decided here: the step-by-step kernel takes the query
+  if (threadIdx.x == 0) over_list[atomicAdd(over_n, 1u)] = e;
+  return;
+out:
+  for (int i = (int)threadIdx.x; i < k; i += KS_T) {
+    const bool ok = (uint32_t)i < mb;
+    oi[i] = ok ? (int32_t)s_bid[i] : -1;
+    if (od) od[i] = ok ? s_d[i] : INFINITY;
+  }
 }
 
 }  // namespace
@@ -1151,10 +1492,32 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   if (nq < 0 || nq >= (int64_t)0x7fffffff) return fail(CG_ERR_INVALID, "nq out of range");
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external k-NN queries on a batched index (every point queries its own tile)");
-  // small batches: one warp per query, Algorithm 2 with the density step
-  // (the same result), no query plan
-  if (!all_points && nq > 0 && nq <= kSmallBatch)
-    return knn_grow_pass(ix, q, nq, k, 1, idx, d2, nullptr, st, C.status);
+  // small batches: one block per query, no query plan; the queries it
+  // cannot decide (boxes or bands too large for its shared memory) run
+  // Algorithm 2 step by step with the density rule (the same result)
+  if (!all_points && nq > 0 && nq <= kSmallBatch && ix->ntiles == 1) {
+    DevBufs tmp;
+    uint32_t* over = (uint32_t*)tmp.get(4 * (size_t)nq + 64, st);
+    if (!over) return fail(CG_ERR_OOM, "device allocation failed (small k-NN)");
+    uint32_t* over_n = over + nq;
+    cudaError_t e = cudaMemsetAsync(over_n, 0, 4, st);
+    if (e == cudaSuccess) {
+      ProfScope prof("knn_small", st);
+      if (ix->precision == CG_FP32_OFFSET)
+        knn_small_kernel<1><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, over, over_n, C.status);
+      else
+        knn_small_kernel<0><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, over, over_n, C.status);
+      note_launch();
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      tmp.release(st);
+      return cuda_fail(e, "small k-NN kernel");
+    }
+    cg_status s = knn_grow_pass(ix, q, nq, k, 1, idx, d2, nullptr, st, C.status, over, over_n);
+    tmp.release(st);
+    return s;
+  }
   if (!all_points) {
     cg_status s = prepare_queries(ix, C, q, nq, false, st);
     if (s != CG_OK) return s;
@@ -1248,7 +1611,8 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
 
 
 cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
-                        int64_t* visited, cudaStream_t st, uint32_t* status) {
+                        int64_t* visited, cudaStream_t st, uint32_t* status, const uint32_t* list,
+                        const uint32_t* list_n) {
   if (!status) status = ix->status;
   if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
   if (policy != 0 && policy != 1) return fail(CG_ERR_INVALID, "policy must be 0 (monotone) or 1 (density)");
@@ -1265,10 +1629,10 @@ cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int po
   ProfScope prof("knn_grow", st);
   if (ix->precision == CG_FP32_OFFSET)
     knn_grow_kernel<1><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
-                                             reinterpret_cast<long long*>(visited), status);
+                                             reinterpret_cast<long long*>(visited), status, list, list_n);
   else
     knn_grow_kernel<0><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
-                                             reinterpret_cast<long long*>(visited), status);
+                                             reinterpret_cast<long long*>(visited), status, list, list_n);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k-NN growth kernel");

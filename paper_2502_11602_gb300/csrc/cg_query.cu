@@ -726,17 +726,29 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
   if (!all_points && ix->ntiles != 1)
     return fail(CG_ERR_UNIMPLEMENTED, "external queries on a batched index");
   RadiusState& R = C.radius;
-  // small batches: one warp per query, no plan (the count reads its sizes
+  // small batches: one block per query, no plan (the count reads its sizes
   // back, so it is taken only when the caller asks for the total)
   if (!all_points && ix->ntiles == 1 && nq > 0 && nq <= kSmallBatch && (fill ? R.small : total_host != nullptr)) {
     if (!fill) {
       R.bufs.release(st);
       R.valid = false;
       R.small = false;
-      uint32_t* counts = (uint32_t*)R.bufs.get(4 * (size_t)nq, st);
-      uint32_t* stats = (uint32_t*)R.bufs.get(64, st);
-      if (!counts || !stats) return fail(CG_ERR_OOM, "device allocation failed (small radius pass)");
-      cudaError_t e = launch_small_count(ix->view(), kernel, q, (uint32_t)nq, r, counts, offsets, stats, C.status, st);
+      if (!R.small_counts) {
+        R.small_counts = (uint32_t*)R.small_bufs.get(4 * (size_t)kSmallBatch, st);
+        R.small_stats = (uint32_t*)R.small_bufs.get(64, st);
+        R.small_rows = (int32_t*)R.small_bufs.get(4 * (size_t)kSmallRowCap * (size_t)kSmallBatch, st);
+        if (!R.small_counts || !R.small_stats || !R.small_rows) {
+          R.small_bufs.release(st);
+          R.small_counts = R.small_stats = nullptr;
+          R.small_rows = nullptr;
+          return fail(CG_ERR_OOM, "device allocation failed (small radius pass)");
+        }
+      }
+      uint32_t* counts = R.small_counts;
+      uint32_t* stats = R.small_stats;
+      int32_t* rows = R.small_rows;
+      cudaError_t e =
+          launch_small_count(ix->view(), kernel, q, (uint32_t)nq, r, counts, rows, offsets, stats, C.status, st);
       uint32_t maxrow = 0, w = 0;
       HostRead rd;
       rd.get(total_host, offsets + nq, 8);
@@ -761,7 +773,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
     } else {
       if (!R.valid || R.all_points || R.q != q || R.nq != nq || R.r != r || R.kernel != kernel)
         return fail(CG_ERR_INVALID, "radius fill without a matching count pass");
-      cudaError_t e = launch_small_fill(ix->view(), kernel, q, (uint32_t)nq, r, offsets, out, C.status, st);
+      cudaError_t e = launch_small_fill(R.small_rows, (uint32_t)nq, offsets, out, C.status, st);
       if (e != cudaSuccess) return cuda_fail(e, "small radius fill");
       return CG_OK;
     }

@@ -185,15 +185,90 @@ inline bool zw_applies(const cg_index* ix, int kern) {
 
 // Small query batches (cg_small.cu): one block per query, no plan.  Calls of
 // up to kSmallBatch external queries take this path when their rows are at
-// most kSmallRowCap long (checked by the count).
+// most kSmallRowCap long (checked by the count, which also writes the rows
+// to a scratch buffer of kSmallRowCap entries per query; the fill copies).
 constexpr int64_t kSmallBatch = 1024;
 constexpr int kSmallRowCap = 2048;
 cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
-                               uint32_t* counts, int64_t* offsets, uint32_t* stats, uint32_t* status,
-                               cudaStream_t st);
-cudaError_t launch_small_fill(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
-                              const int64_t* offsets, int32_t* out, uint32_t* status, cudaStream_t st);
+                               uint32_t* counts, int32_t* rows, int64_t* offsets, uint32_t* stats,
+                               uint32_t* status, cudaStream_t st);
+cudaError_t launch_small_fill(const int32_t* rows, uint32_t nq, const int64_t* offsets, int32_t* out,
+                              uint32_t* status, cudaStream_t st);
 
 QuerySet query_set(cg_index* ix, const double* q, int64_t nq, bool all_points);
+
+// The sorted points of a voxel box [lo, hi] (one contiguous span per grid
+// row of a 2D grid, per (i, j) column of a 3D grid), visited by a whole
+// block of kBoxThreads threads: the spans of up to kBoxThreads rows or
+// columns are looked up at once, then every thread takes candidates
+// threadIdx.x, + kBoxThreads, ... of their concatenation, so that all the
+// loads of a box are in flight together.  f(t, valid) is called by every
+// thread the same number of times (valid false past the end), t the sorted
+// position; s_start / s_off are kBoxThreads + 1 words of shared memory.
+constexpr int kBoxThreads = 256;
+template <class F>
+__device__ __forceinline__ void for_each_in_box(const IndexView& ix, const Tile& T, const int* lo, const int* hi,
+                                                uint32_t* s_start, uint32_t* s_off, F f) {
+  const int nax = ix.dim;
+  const int ni = hi[0] - lo[0] + 1, nj = hi[1] - lo[1] + 1;
+  const int nsp = nax == 2 ? ni : ni * nj;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  for (int b0 = 0; b0 < nsp; b0 += kBoxThreads) {
+    const int nb = min(kBoxThreads, nsp - b0);
+    __syncthreads();  // the previous batch's spans are no longer read
+    uint32_t len = 0;
+    if ((int)threadIdx.x < nb) {
+      const int sidx = b0 + (int)threadIdx.x;
+      uint32_t k0, k1;
+      if (nax == 2) {
+        const uint32_t row = (uint32_t)(lo[0] + sidx) * (uint32_t)T.n[1];
+        k0 = T.key_base + row + (uint32_t)lo[1];
+        k1 = T.key_base + row + (uint32_t)hi[1];
+      } else {
+        const int i = lo[0] + sidx / nj, j = lo[1] + sidx % nj;
+        const uint32_t col = ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) * (uint32_t)T.n[2];
+        k0 = T.key_base + col + (uint32_t)lo[2];
+        k1 = T.key_base + col + (uint32_t)hi[2];
+      }
+      const uint2 sp = row_span(ix, T, k0, k1);
+      s_start[threadIdx.x] = sp.x;
+      len = sp.y - sp.x;
+    }
+    // exclusive scan of the lengths over the block (s_off[nb] = total)
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_off[kBoxThreads - 1 - warp] = incl;  // warp totals, parked at the end
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+    for (uint32_t w = 0; w < kBoxThreads / 32; ++w) {
+      const uint32_t x = s_off[kBoxThreads - 1 - w];
+      wbase += w < warp ? x : 0u;
+      total += x;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb) s_off[threadIdx.x] = wbase + incl - len;
+    if (threadIdx.x == 0) s_off[nb] = total;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < total; c0 += kBoxThreads) {
+      const uint32_t c = c0 + threadIdx.x;
+      const bool valid = c < total;
+      uint32_t t = 0;
+      if (valid) {
+        int a = 0, b = nb - 1;  // the span holding candidate c
+        while (a < b) {
+          const int m = (a + b + 1) >> 1;
+          if (s_off[m] <= c) a = m;
+          else b = m - 1;
+        }
+        t = s_start[a] + (c - s_off[a]);
+      }
+      f(t, valid);
+    }
+  }
+}
 
 }  // namespace cg

@@ -9,15 +9,20 @@
 // flight) and runs Algorithm 1 for it as stated: the voxel range of the
 // kernel's bounding box (widened by one voxel on each side, so that the
 // rounding of the voxel keys can never hide a point), every point of those
-// voxels tested with the exact binary64 predicate.  A voxel row (2D) or
-// column (3D) of consecutive keys is one contiguous run of sorted points.
+// voxels tested.  A voxel row (2D) or column (3D) of consecutive keys is one
+// contiguous run of sorted points.  A candidate costs one load of its sorted
+// record: binary32 offsets are screened with the thresholds of the regular
+// path (computed per query from the query's own encode bound) and only the
+// band between them is decided on the exact binary64 coordinates; binary64
+// records are decided on the record itself.
 //
-//   count  per query, the number of points inside; then one block scans the
-//          counts into offsets and records the largest row.
-//   fill   per query, the ids of the points inside, gathered in shared
-//          memory, sorted ascending (bitonic, the whole block) and written
-//          out; rows longer than the shared buffer are refused on the host
-//          (the caller then takes the regular path).
+//   count  per query, the ids of the points inside gathered in shared
+//          memory, sorted ascending (bitonic, the whole block), written to a
+//          scratch row of kSmallRowCap entries, and their number; then one
+//          block scans the numbers into offsets and records the largest row
+//          (rows longer than the scratch row are refused on the host, and
+//          the caller then takes the regular path).
+//   fill   copies each scratch row to its place in the CSR output.
 #include <math.h>
 
 #include <algorithm>
@@ -28,7 +33,7 @@
 namespace cg {
 namespace {
 
-constexpr int SW = 4;  // warps per block
+constexpr int SW = kBoxThreads / 32;  // warps per block
 
 // The voxel range of the kernel's box on axis a, from binary64 (the
 // oracle's formula); false when it misses the grid.
@@ -41,70 +46,142 @@ __device__ __forceinline__ bool small_range(const Tile& T, int a, double c, doub
   return true;
 }
 
-// Calls f(t0, t1) for every contiguous run of sorted points the kernel of
-// query c can reach (warp-uniform); returns false if a coordinate is not
-// finite.
-template <int KERN, class F>
-__device__ __forceinline__ bool small_runs(const IndexView& ix, const double* c, double r, F f) {
+// The voxel box of query c's kernel (Algorithm 1's range, widened by one
+// voxel); false when a coordinate is not finite, an empty box (lo > hi)
+// when it misses the grid.
+template <int KERN>
+__device__ __forceinline__ bool small_box(const IndexView& ix, const double* cx, double r, int* lo, int* hi) {
   const Tile& T = ix.tiles[0];
-  const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
   if (!(isfinite(cx[0]) && isfinite(cx[1]) && isfinite(cx[2]))) return false;
-  int lo[3], hi[3];
+  lo[2] = 0;
+  hi[2] = T.n[2] - 1;
   for (int a = 0; a < 2; ++a)
-    if (!small_range(T, a, cx[a], r, lo[a], hi[a])) return true;
-  if (ix.dim == 3) {
-    if (KERN == CG_CYLINDER) {  // z unbounded: every slice of the columns
-      lo[2] = 0;
-      hi[2] = T.n[2] - 1;
-    } else if (!small_range(T, 2, cx[2], r, lo[2], hi[2])) {
+    if (!small_range(T, a, cx[a], r, lo[a], hi[a])) {
+      lo[0] = 1;
+      hi[0] = 0;
       return true;
     }
+  if (ix.dim == 3 && KERN != CG_CYLINDER && !small_range(T, 2, cx[2], r, lo[2], hi[2])) {
+    lo[0] = 1;
+    hi[0] = 0;
   }
-  for (int i = lo[0]; i <= hi[0]; ++i) {
-    if (ix.dim == 2) {
-      const uint32_t row = T.key_base + (uint32_t)i * (uint32_t)T.n[1];
-      const uint2 sp = row_span(ix, T, row + (uint32_t)lo[1], row + (uint32_t)hi[1]);
-      if (sp.y > sp.x) f(sp.x, sp.y);
-    } else {
-      for (int j = lo[1]; j <= hi[1]; ++j) {
-        const uint32_t col = T.key_base + ((uint32_t)i * (uint32_t)T.n[1] + (uint32_t)j) * (uint32_t)T.n[2];
-        const uint2 sp = row_span(ix, T, col + (uint32_t)lo[2], col + (uint32_t)hi[2]);
-        if (sp.y > sp.x) f(sp.x, sp.y);
-      }
-    }
-  }
-  return true;
+  return true;  // the cylinder is unbounded in z: every slice of the columns
 }
 
-__device__ __forceinline__ uint32_t small_id(const IndexView& ix, uint32_t t) {
-  return ix.precision == CG_FP32_OFFSET ? __float_as_uint(__ldg(&ix.pts32[t].w))
-                                        : (uint32_t)__double_as_longlong(ix.pts64s[t].w);
+// One query's screen: its binary32 offsets in the index's frame and the
+// decision thresholds from its own encode bound (the regular path's
+// formulas, with the query set reduced to this query).
+struct SmallQuery {
+  float4 qf;      // x~, y~, z~ of the query
+  Thresholds thr;
+};
+
+__device__ __forceinline__ void small_query(const Tile& T, const double* cx, double r, SmallQuery& S) {
+  const float x = __double2float_rn(__dsub_rn(cx[0], T.origin[0]));
+  const float y = __double2float_rn(__dsub_rn(cx[1], T.origin[1]));
+  const float z = __double2float_rn(__dsub_rn(cx[2], T.origin[2]));
+  S.qf = make_float4(x, y, z, 0.f);
+  const double m = (double)fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+  const double e_q = ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30;
+  S.thr = make_thresholds(r, (double)T.enc_err, e_q);
 }
 
+// Is sorted record t inside the kernel around the query?  Binary32 records:
+// the screen, then binary64 in the band; binary64 records: exact.
 template <int KERN>
+__device__ __forceinline__ bool small_in(const IndexView& ix, uint32_t t, const SmallQuery& S, const double* c,
+                                         uint32_t& id) {
+  if (ix.precision == CG_FP32_OFFSET) {
+    const float4 p = __ldg(&ix.pts32[t]);
+    id = __float_as_uint(p.w);
+    const float dx = __fsub_rn(p.x, S.qf.x), dy = __fsub_rn(p.y, S.qf.y), dz = __fsub_rn(p.z, S.qf.z);
+    float v, lo, hi;
+    if (KERN == CG_CUBE) {
+      v = fmaxf(fmaxf(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+      lo = S.thr.c_lo;
+      hi = S.thr.c_hi;
+    } else {
+      v = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+      if (KERN == CG_SPHERE) v = __fmaf_rn(dz, dz, v);
+      lo = S.thr.s_lo;  // the cylinder's two-term value: the sphere's band bounds it
+      hi = S.thr.s_hi;
+    }
+    if (v <= lo) return true;
+    if (v > hi) return false;
+    return exact_in<KERN>(ix.xyz64 + 3 * (size_t)id, c, S.thr.r2);
+  }
+  const double4_32a p = ix.pts64s[t];
+  id = (uint32_t)__double_as_longlong(p.w);
+  const double4_32a cc = make_double4_32a(__ldg(c), __ldg(c + 1), __ldg(c + 2), 0.0);
+  return exact_in4<KERN>(p, cc, S.thr.r2);
+}
+
+// Count + gather: block e takes query e; its ids inside (at most CAP kept),
+// sorted ascending, go to rows[e * CAP ...]; counts[e] = their number.
+template <int KERN, int CAP>
 __global__ void __launch_bounds__(SW * 32) small_count_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                               double r, uint32_t* __restrict__ counts,
-                                                              uint32_t* status) {
-  __shared__ uint32_t wsum[SW];
-  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+                                                              int32_t* __restrict__ rows, uint32_t* status) {
+  __shared__ uint32_t B[CAP];
+  __shared__ uint32_t s_start[kBoxThreads + 1], s_off[kBoxThreads + 1];
+  __shared__ uint32_t nhit;
+  __shared__ int s_box[7];  // lo[3], hi[3], coordinates finite
+  __shared__ SmallQuery S;
   const uint32_t e = blockIdx.x;
   if (e >= nq) return;
   const double* c = q + 3 * (size_t)e;
-  const double r2 = __dmul_rn(r, r);
-  uint32_t cnt = 0;
-  const bool ok = small_runs<KERN>(ix, c, r, [&](uint32_t t0, uint32_t t1) {
-    for (uint32_t t = t0 + threadIdx.x; t < t1; t += SW * 32)
-      cnt += exact_in<KERN>(ix.xyz64 + 3 * (size_t)small_id(ix, t), c, r2) ? 1u : 0u;
-  });
-  cnt = __reduce_add_sync(0xffffffffu, cnt);
-  if (lane == 0) wsum[w] = cnt;
+  if (threadIdx.x == 0) {  // binary64 set-up on one thread (the binary64 pipe is narrow)
+    nhit = 0;
+    const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
+    small_query(ix.tiles[0], cx, r, S);
+    int l0[3] = {1, 1, 1}, h0[3] = {0, 0, 0};
+    s_box[6] = small_box<KERN>(ix, cx, r, l0, h0) ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+      s_box[a] = l0[a];
+      s_box[3 + a] = h0[a];
+    }
+  }
   __syncthreads();
+  const SmallQuery Q = S;
+  const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
+  const bool ok = s_box[6] != 0;
+  if (ok && lo[0] <= hi[0])
+    for_each_in_box(ix, ix.tiles[0], lo, hi, s_start, s_off, [&](uint32_t t, bool valid) {
+      uint32_t id = 0;
+      const bool in = valid && small_in<KERN>(ix, t, Q, c, id);
+      const unsigned bm = __ballot_sync(0xffffffffu, in);
+      uint32_t base = 0;
+      if ((threadIdx.x & 31u) == 0 && bm) base = atomicAdd(&nhit, (uint32_t)__popc(bm));
+      base = __shfl_sync(0xffffffffu, base, 0) + __popc(bm & lanemask_lt());
+      if (in && base < (uint32_t)CAP) B[base] = id;
+    });
+  __syncthreads();
+  const uint32_t n = ok ? nhit : 0u;
   if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-    for (int i = 0; i < SW; ++i) tot += wsum[i];
-    counts[e] = ok ? tot : 0u;
+    counts[e] = n;
     if (!ok) atomicOr(status, ST_NONFINITE);
   }
+  if (n > (uint32_t)CAP) return;  // refused on the host: nothing to sort
+  uint32_t n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (uint32_t i = n + threadIdx.x; i < n2; i += SW * 32) B[i] = 0xffffffffu;
+  __syncthreads();
+  for (uint32_t k = 2; k <= n2; k <<= 1)  // bitonic sort of the row, ascending
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n2; i += SW * 32) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint32_t a = B[i], b = B[l];
+          if (((i & k) == 0) ? a > b : a < b) {
+            B[i] = b;
+            B[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  int32_t* row = rows + (size_t)e * CAP;
+  for (uint32_t i = threadIdx.x; i < n; i += SW * 32) row[i] = (int32_t)B[i];
 }
 
 // One block: offsets = exclusive scan of counts (offsets[nq] = total), and
@@ -143,53 +220,20 @@ __global__ void __launch_bounds__(1024) small_scan_kernel(const uint32_t* __rest
   if (t == nq - 1) offsets[nq] = (int64_t)(ex + v);
 }
 
-template <int KERN, int CAP>
-__global__ void __launch_bounds__(SW * 32) small_fill_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
-                                                             double r, const int64_t* __restrict__ offsets,
+// Block e copies scratch row e to its place in the CSR output.
+template <int CAP>
+__global__ void __launch_bounds__(SW * 32) small_copy_kernel(const int32_t* __restrict__ rows, uint32_t nq,
+                                                             const int64_t* __restrict__ offsets,
                                                              int32_t* __restrict__ out, uint32_t* status) {
-  __shared__ uint32_t B[CAP];
-  __shared__ uint32_t nhit;
   const uint32_t e = blockIdx.x;
   if (e >= nq) return;
-  const double* c = q + 3 * (size_t)e;
-  const double r2 = __dmul_rn(r, r);
-  if (threadIdx.x == 0) nhit = 0;
-  __syncthreads();
-  small_runs<KERN>(ix, c, r, [&](uint32_t t0, uint32_t t1) {
-    for (uint32_t t = t0 + threadIdx.x; t < t1; t += SW * 32) {
-      const uint32_t id = small_id(ix, t);
-      if (exact_in<KERN>(ix.xyz64 + 3 * (size_t)id, c, r2)) {
-        const uint32_t at = atomicAdd(&nhit, 1u);
-        if (at < (uint32_t)CAP) B[at] = id;
-      }
-    }
-  });
-  __syncthreads();
-  const uint32_t n = nhit;
-  const int64_t o0 = offsets[e];
-  if ((int64_t)n != offsets[e + 1] - o0 || n > (uint32_t)CAP) {  // count and fill disagree, or too long
+  const int64_t o0 = offsets[e], n = offsets[e + 1] - o0;
+  if (n < 0 || n > CAP) {  // offsets not from this count
     if (threadIdx.x == 0) atomicOr(status, ST_INTERNAL);
     return;
   }
-  uint32_t n2 = 1;
-  while (n2 < n) n2 <<= 1;
-  for (uint32_t i = n + threadIdx.x; i < n2; i += SW * 32) B[i] = 0xffffffffu;
-  __syncthreads();
-  for (uint32_t k = 2; k <= n2; k <<= 1)  // bitonic sort of the row, ascending
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < n2; i += SW * 32) {
-        const uint32_t l = i ^ j;
-        if (l > i) {
-          const uint32_t a = B[i], b = B[l];
-          if (((i & k) == 0) ? a > b : a < b) {
-            B[i] = b;
-            B[l] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  for (uint32_t i = threadIdx.x; i < n; i += SW * 32) out[o0 + i] = (int32_t)B[i];
+  const int32_t* row = rows + (size_t)e * CAP;
+  for (int64_t i = threadIdx.x; i < n; i += SW * 32) out[o0 + i] = row[i];
 }
 
 }  // namespace
@@ -197,29 +241,26 @@ __global__ void __launch_bounds__(SW * 32) small_fill_kernel(IndexView ix, const
 // ------------------------------------------------------------------ host
 
 cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
-                               uint32_t* counts, int64_t* offsets, uint32_t* stats, uint32_t* status,
-                               cudaStream_t st) {
+                               uint32_t* counts, int32_t* rows, int64_t* offsets, uint32_t* stats,
+                               uint32_t* status, cudaStream_t st) {
   const int grid = (int)nq;  // a block per query
   ProfScope prof("radius_small_count", st);
-  if (kern == CG_SPHERE) small_count_kernel<CG_SPHERE><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, status);
-  else if (kern == CG_CUBE) small_count_kernel<CG_CUBE><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, status);
-  else small_count_kernel<CG_CYLINDER><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, status);
+  if (kern == CG_SPHERE)
+    small_count_kernel<CG_SPHERE, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, rows, status);
+  else if (kern == CG_CUBE)
+    small_count_kernel<CG_CUBE, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, rows, status);
+  else
+    small_count_kernel<CG_CYLINDER, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, counts, rows, status);
   note_launch();
   small_scan_kernel<<<1, 1024, 0, st>>>(counts, nq, offsets, stats);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_small_fill(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
-                              const int64_t* offsets, int32_t* out, uint32_t* status, cudaStream_t st) {
-  const int grid = (int)nq;  // a block per query
+cudaError_t launch_small_fill(const int32_t* rows, uint32_t nq, const int64_t* offsets, int32_t* out,
+                              uint32_t* status, cudaStream_t st) {
   ProfScope prof("radius_small_fill", st);
-  if (kern == CG_SPHERE)
-    small_fill_kernel<CG_SPHERE, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, offsets, out, status);
-  else if (kern == CG_CUBE)
-    small_fill_kernel<CG_CUBE, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, offsets, out, status);
-  else
-    small_fill_kernel<CG_CYLINDER, kSmallRowCap><<<grid, SW * 32, 0, st>>>(iv, q, nq, r, offsets, out, status);
+  small_copy_kernel<kSmallRowCap><<<(int)nq, SW * 32, 0, st>>>(rows, nq, offsets, out, status);
   note_launch();
   return cudaGetLastError();
 }

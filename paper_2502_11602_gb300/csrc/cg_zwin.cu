@@ -189,39 +189,62 @@ __global__ void __launch_bounds__(256) zsort_long_kernel(const float4* __restric
 template <class Emit>
 __device__ __forceinline__ uint32_t z_chunks_of_run(const float4* __restrict__ pz, uint32_t s, uint32_t e,
                                                     float dz, uint32_t qmax, Emit emit) {
+  // one warp per run: the next chunk starts at the first point, at or after
+  // the current chunk's next candidate, that is qmax points past the chunk's
+  // first or more than dz above it; 32 points tested per step (a ballot).
+  // The same chunks as a point-by-point scan (the tests are identical and
+  // taken in the same order).  Chunk c starting at point i: emit(c, i),
+  // called by lane 0.
+  const uint32_t lane = threadIdx.x & 31u;
   if (e <= s) return 0u;
   const bool sorted = e - s <= kZsortMax;
   uint32_t c = 0, start = s;
   float z0 = pz[s].z;
-  emit(0u, s);
-  for (uint32_t i = s + 1; i < e; ++i) {
-    const float z = sorted ? pz[i].z : z0;
-    if (i - start >= qmax || z - z0 > dz) {
-      start = i;
-      z0 = z;
-      emit(++c, i);
+  if (lane == 0) emit(0u, s);
+  for (uint32_t i0 = s + 1; i0 < e;) {
+    const uint32_t i = i0 + lane;
+    bool brk = false;
+    float z = z0;
+    if (i < e) {
+      z = sorted ? pz[i].z : z0;
+      brk = i - start >= qmax || z - z0 > dz;
     }
+    const unsigned bm = __ballot_sync(0xffffffffu, brk);
+    if (bm == 0u) {
+      i0 += 32u;
+      continue;
+    }
+    const int src = __ffs(bm) - 1;
+    start = i0 + (uint32_t)src;
+    z0 = __shfl_sync(0xffffffffu, z, src);
+    ++c;
+    if (lane == 0) emit(c, start);
+    i0 = start + 1u;
   }
   return c + 1u;
 }
 
 __global__ void zchunk_count_kernel(const float4* __restrict__ pz, const uint32_t* __restrict__ ustart,
                                     uint32_t nruns, float dz, uint32_t qmax, uint32_t* __restrict__ cnt) {
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x)
-    cnt[r] = z_chunks_of_run(pz, ustart[r], ustart[r + 1], dz, qmax, [](uint32_t, uint32_t) {});
+  const uint32_t lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nruns; r += nw) {
+    const uint32_t c = z_chunks_of_run(pz, ustart[r], ustart[r + 1], dz, qmax, [](uint32_t, uint32_t) {});
+    if (lane == 0) cnt[r] = c;
+  }
 }
 
 __global__ void zchunk_emit_kernel(const float4* __restrict__ pz, const uint32_t* __restrict__ ustart,
                                    const uint32_t* __restrict__ ukeys, uint32_t nruns, float dz, uint32_t qmax,
                                    const uint32_t* __restrict__ coff, uint32_t* __restrict__ cbeg,
                                    uint32_t* __restrict__ ckey, uint32_t n) {
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u, nw = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nruns; r += nw) {
     const uint32_t o = coff[r], key = ukeys[r];
     z_chunks_of_run(pz, ustart[r], ustart[r + 1], dz, qmax, [&](uint32_t c, uint32_t i) {
       cbeg[o + c] = i;
       ckey[o + c] = key;
     });
-    if (r == nruns - 1) cbeg[coff[nruns]] = n;
+    if (r == nruns - 1 && lane == 0) cbeg[coff[nruns]] = n;
   }
 }
 
@@ -263,7 +286,7 @@ cudaError_t launch_zsort(const float4* in, float4* out, uint32_t* sid_out, const
 cudaError_t launch_zchunk_count(const float4* pz, const uint32_t* ustart, uint32_t nruns, float dz, uint32_t qmax,
                                 uint32_t* cnt, cudaStream_t st) {
   if (nruns == 0) return cudaSuccess;
-  const int g = (int)std::min<int64_t>(((int64_t)nruns + 255) / 256, (int64_t)zw_sm_count() * 8);
+  const int g = (int)std::min<int64_t>(((int64_t)nruns + 7) / 8, (int64_t)zw_sm_count() * 8);
   zchunk_count_kernel<<<g, 256, 0, st>>>(pz, ustart, nruns, dz, qmax, cnt);
   note_launch();
   return cudaGetLastError();
@@ -273,7 +296,7 @@ cudaError_t launch_zchunk_emit(const float4* pz, const uint32_t* ustart, const u
                                float dz, uint32_t qmax, const uint32_t* coff, uint32_t* cbeg, uint32_t* ckey,
                                uint32_t n, cudaStream_t st) {
   if (nruns == 0) return cudaSuccess;
-  const int g = (int)std::min<int64_t>(((int64_t)nruns + 255) / 256, (int64_t)zw_sm_count() * 8);
+  const int g = (int)std::min<int64_t>(((int64_t)nruns + 7) / 8, (int64_t)zw_sm_count() * 8);
   zchunk_emit_kernel<<<g, 256, 0, st>>>(pz, ustart, ukeys, nruns, dz, qmax, coff, cbeg, ckey, n);
   note_launch();
   return cudaGetLastError();
