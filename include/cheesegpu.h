@@ -186,6 +186,25 @@ cg_status cg_radius_fill(cg_index_t index, const double* q_dev, int64_t nq, doub
                          void* stream);
 
 /*
+ * cg_radius_search_into -- both passes of the kernel search of Algorithm 1
+ * (Section 3.4.1) into the caller's buffers, one call: the count, then, if
+ * the total fits `capacity`, the fill.
+ *  offsets_dev  device int64 [nq+1], written as by cg_radius_count.
+ *  indices_dev  device int32 [capacity]; rows as by cg_radius_fill.
+ *  capacity     entries of indices_dev (>= 0).
+ *  total_host   host int64, set to offsets[nq] on CG_OK and on
+ *               CG_ERR_OVERFLOW.
+ * Returns CG_ERR_OVERFLOW when the total exceeds the capacity: the count
+ * stands, and cg_radius_fill with the same arguments and a buffer of
+ * *total_host entries completes the search.  Batches of up to 1024 queries
+ * cost one stream synchronisation (the rows are copied with the count);
+ * larger ones two.  Other arguments and errors as cg_radius_count.
+ */
+cg_status cg_radius_search_into(cg_index_t index, const double* q_dev, int64_t nq, double r,
+                                cg_kernel kernel, int64_t* offsets_dev, int32_t* indices_dev,
+                                int64_t capacity, int64_t* total_host, void* stream);
+
+/*
  * cg_radius_search -- both passes of the kernel search of Algorithm 1
  * (Section 3.4.1): count + scan + fill, with outputs allocated by the
  * library (hook or cudaMallocAsync); the caller releases them with

@@ -30,13 +30,18 @@ STATUS = {0: "CG_OK", 1: "CG_ERR_INVALID", 2: "CG_ERR_OOM", 3: "CG_ERR_CUDA", 4:
 
 EXPORTS = ["cg_set_allocator", "cg_last_error", "cg_version", "cg_launch_count", "cg_build", "cg_build_batched",
            "cg_index_info", "cg_index_status", "cg_index_free", "cg_radius_count", "cg_radius_fill", "cg_radius_search",
-           "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
+           "cg_radius_search_into", "cg_free_device", "cg_all_points_count", "cg_all_points_fill", "cg_knn",
            "cg_all_points_knn", "cg_knn_grow", "cg_offsets_scan_noalloc", "cg_pipeline_create", "cg_pipeline_run",
            "cg_pipeline_outputs", "cg_pipeline_info", "cg_pipeline_free", "cg_server_create", "cg_server_submit",
            "cg_server_wait", "cg_server_wait_any", "cg_server_release", "cg_server_stats", "cg_server_free",
            "cg_profile_enable", "cg_profile_read", "cg_set_tuning", "cg_get_tuning", "cg_radius_stats"]
 
 REQ_RADIUS, REQ_KNN = 0, 1
+
+# The library's small-batch paths: calls of up to SMALL_BATCH external
+# queries, rows of up to SMALL_ROW_CAP neighbours kept per query.
+SMALL_BATCH, SMALL_ROW_CAP = 1024, 2048
+SMALL_GUESS = 256  # output entries reserved per query by a small radius call
 
 
 class CheeseError(RuntimeError):
@@ -158,6 +163,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "cg_radius_count": [P, P, I64, D, I, P, P, P],
             "cg_radius_fill": [P, P, I64, D, I, P, P, P],
             "cg_radius_search": [P, P, I64, D, I, P, P, P, P],
+            "cg_radius_search_into": [P, P, I64, D, I, P, P, I64, P, P],
             "cg_free_device": [P, P],
             "cg_all_points_count": [P, D, I, P, P, P],
             "cg_all_points_fill": [P, D, I, P, P, P],
@@ -209,8 +215,12 @@ def _ptr(t) -> int | None:
 
 
 def _stream(stream=None) -> int:
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return s.cuda_stream
+    if stream is not None:
+        return stream.cuda_stream
+    raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)  # the current stream's handle, without a Stream object
+    if raw is not None:
+        return raw(torch.cuda.current_device())
+    return torch.cuda.current_stream().cuda_stream
 
 
 def _points(x: torch.Tensor) -> torch.Tensor:
@@ -273,6 +283,18 @@ def cg_radius_count(h, q, r, kernel, offsets, want_total=True, stream=None):
     _check(load().cg_radius_count(h, _ptr(q), q.shape[0], float(r), kernel, _ptr(offsets),
                                   ctypes.byref(tot) if want_total else None, _stream(stream)))
     return tot.value if want_total else None
+
+
+def cg_radius_search_into(h, q, r, kernel, offsets, indices, capacity, stream=None):
+    """Count + fill into `indices` (capacity entries): (fits, total).  When the
+    rows do not fit, the count stands and cg_radius_fill completes it."""
+    tot = ctypes.c_int64(0)
+    rc = load().cg_radius_search_into(h, _ptr(q), q.shape[0], float(r), kernel, _ptr(offsets), _ptr(indices),
+                                      int(capacity), ctypes.byref(tot), _stream(stream))
+    if rc == 5:  # CG_ERR_OVERFLOW
+        return False, tot.value
+    _check(rc)
+    return True, tot.value
 
 
 def cg_radius_fill(h, q, r, kernel, offsets, indices, stream=None):
@@ -562,6 +584,21 @@ class Index:
                       check: bool = True):
         """CSR (offsets int64 [nq+1], indices int32 [total]); q=None: every point."""
         nq = self.n if q is None else q.shape[0]
+        if q is not None and 0 < nq <= SMALL_BATCH:
+            # small calls: count and fill in one call (one synchronisation)
+            # into a buffer of SMALL_GUESS entries per query; longer results
+            # take one more (unsynchronised) fill into a buffer of their size
+            q = _points(q)
+            cap = nq * SMALL_GUESS + 1024
+            offsets = torch.empty(nq + 1, dtype=torch.int64, device=self.device)
+            indices = torch.empty(cap, dtype=torch.int32, device=self.device)
+            fits, total = cg_radius_search_into(self.h, q, r, kernel, offsets, indices, cap, stream=stream)
+            if not fits:
+                indices = torch.empty(max(total, 1), dtype=torch.int32, device=self.device)
+                cg_radius_fill(self.h, q, r, kernel, offsets, indices, stream=stream)
+            if check:
+                cg_index_status(self.h, stream)
+            return offsets, indices[:total]
         offsets = torch.empty(nq + 1, dtype=torch.int64, device=self.device)
         if q is None:
             total = cg_all_points_count(self.h, r, kernel, offsets, stream=stream)

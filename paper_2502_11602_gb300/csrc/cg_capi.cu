@@ -571,6 +571,16 @@ cg_status cg_radius_fill(cg_index_t ix, const double* q_dev, int64_t nq, double 
                      nullptr, (cudaStream_t)stream);
 }
 
+cg_status cg_radius_search_into(cg_index_t ix, const double* q_dev, int64_t nq, double r, cg_kernel kernel,
+                                int64_t* offsets_dev, int32_t* indices_dev, int64_t capacity, int64_t* total_host,
+                                void* stream) {
+  if (!ix || !offsets_dev || !total_host || (nq > 0 && !q_dev) || (capacity > 0 && !indices_dev))
+    return fail(CG_ERR_INVALID, "NULL argument");
+  if (capacity < 0) return fail(CG_ERR_INVALID, "capacity must be >= 0");
+  return radius_search_into(ix, ix->ctx, q_dev, nq, r, kernel, offsets_dev, indices_dev, capacity, total_host,
+                            (cudaStream_t)stream);
+}
+
 cg_status cg_all_points_count(cg_index_t ix, double r, cg_kernel kernel, int64_t* offsets_dev,
                               int64_t* total_host, void* stream) {
   if (!ix || !offsets_dev) return fail(CG_ERR_INVALID, "NULL argument");

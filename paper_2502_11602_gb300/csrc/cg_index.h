@@ -89,6 +89,14 @@ struct RadiusState {
   DevBufs small_bufs;
   uint32_t *small_counts = nullptr, *small_stats = nullptr;
   int32_t* small_rows = nullptr;
+  // mapped pinned words the small count writes for the host (total, largest
+  // row, status word): read after a stream sync, no copy launch
+  unsigned long long *small_host = nullptr, *small_host_dev = nullptr;
+  // search-into calls: the small count also copies the rows into the
+  // caller's buffer (when they fit its capacity) before its one sync
+  int32_t* direct_out = nullptr;
+  int64_t direct_cap = 0;
+  bool direct_done = false;
 };
 
 // Mutable state of queries against an index: the external query plan, the
@@ -103,6 +111,10 @@ struct QueryCtx {
     plan.bufs.release(st);
     radius.bufs.release(st);
     radius.small_bufs.release(st);
+    if (radius.small_host) {
+      cudaStreamSynchronize(st);
+      cudaFreeHost(radius.small_host);
+    }
     plan = QueryPlan();
     radius = RadiusState();
   }
@@ -218,6 +230,11 @@ cg_status make_zchunks(cg_index* ix, float dz, uint32_t qmax, DevBufs& bufs, uin
 cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
                       cudaStream_t st);
+// Count and fill into the caller's buffer of `cap` entries (cg_query.cu):
+// CG_ERR_OVERFLOW with *total_host set when the rows do not fit (the count
+// stands; a fill with a larger buffer completes the search).
+cg_status radius_search_into(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, double r, int kernel,
+                             int64_t* offsets, int32_t* out, int64_t cap, int64_t* total_host, cudaStream_t st);
 cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
                    double* d2, cudaStream_t st);
 // Algorithm 2 step by step under a growth policy (0 monotone, 1 density),

@@ -1035,23 +1035,18 @@ __global__ void __launch_bounds__(128) knn_slow_kernel(IndexView ix, QuerySet qs
 // |P^| (the candidates within r) is read off the list: at least k when its
 // k-th entry is within r, else every candidate within r is in the list.  The
 // search ends when |P^| >= k or T covers the grid; visited = |T|.
+// One query (e) of Algorithm 2 step by step, by one warp.
 template <int PREC>
-__global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
-                                                       int k, int policy, int32_t* __restrict__ out_idx,
-                                                       double* __restrict__ out_d2,
-                                                       long long* __restrict__ visited, uint32_t* status,
-                                                       const uint32_t* __restrict__ list, const uint32_t* list_n) {
+__device__ void knn_grow_one(const IndexView& ix, const double* __restrict__ q, uint32_t e, int k, int policy,
+                             int32_t* __restrict__ out_idx, double* __restrict__ out_d2,
+                             long long* __restrict__ visited, uint32_t* status) {
   const unsigned lane = threadIdx.x & 31u;
   const Tile& T = ix.tiles[0];
   const int nax = ix.dim;
   double smin = fmin(T.s[0], T.s[1]);
   if (nax == 3) smin = fmin(smin, T.s[2]);
   const double kPi = 3.14159265358979323846;
-  // every query, or the queries of a list (those another kernel left)
-  const uint32_t nrun = list ? min(*list_n, nq) : nq;
-  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nrun;
-       w += gridDim.x * (blockDim.x / 32)) {
-    const uint32_t e = list ? list[w] : w;
+  {
     const double* c = q + 3 * (size_t)e;
     const double cx[3] = {__ldg(c), __ldg(c + 1), __ldg(c + 2)};
     WarpList L;
@@ -1159,6 +1154,19 @@ __global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const doubl
 }
 
 template <int PREC>
+__global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
+                                                       int k, int policy, int32_t* __restrict__ out_idx,
+                                                       double* __restrict__ out_d2,
+                                                       long long* __restrict__ visited, uint32_t* status,
+                                                       const uint32_t* __restrict__ list, const uint32_t* list_n) {
+  // every query, or the queries of a list (those another kernel left)
+  const uint32_t nrun = list ? min(*list_n, nq) : nq;
+  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nrun;
+       w += gridDim.x * (blockDim.x / 32))
+    knn_grow_one<PREC>(ix, q, list ? list[w] : w, k, policy, out_idx, out_d2, visited, status);
+}
+
+template <int PREC>
 size_t knn_smem() {
   using R = typename KRec<PREC>::T;
   return sizeof(R) * (KRec<PREC>::KMAX + KQB) + KWARPS * LCAP * (8 + 4) + KWARPS * NB * 4 +
@@ -1200,8 +1208,8 @@ __global__ void knn_thr_tiles_kernel(Thresholds* out, const Tile* __restrict__ t
 // true k nearest all lie within sqrt(kth) (the box already holds k points
 // that close), and the voxel range of Algorithm 1 for that radius is
 // gathered and searched once more (final).  A box of more than KS_CAP
-// points or a band wider than KS_BAND sends the query to the step-by-step
-// kernel (the overflow list).
+// points or a band wider than KS_BAND: the block's first warp runs
+// Algorithm 2 step by step for the query instead.
 constexpr int KS_T = kBoxThreads;
 constexpr int KS_CAP = 4096;
 constexpr int KS_BAND = 256;
@@ -1210,8 +1218,8 @@ constexpr int KS_MAX_RING = 64;
 template <int PREC>
 __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                          int k, int32_t* __restrict__ out_idx,
-                                                         double* __restrict__ out_d2, uint32_t* __restrict__ over_list,
-                                                         uint32_t* over_n, uint32_t* status) {
+                                                         double* __restrict__ out_d2, uint32_t* status, float m_host,
+                                                         float alpha_host, float eq_host) {
   using R = typename KRec<PREC>::T;
   __shared__ float s_f[KS_CAP];
   __shared__ uint32_t s_id[KS_CAP];
@@ -1219,7 +1227,10 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
   __shared__ uint32_t s_bid[KS_BAND];
   __shared__ uint32_t s_red[KS_T / 32];
   __shared__ uint32_t s_start[kBoxThreads + 1], s_off[kBoxThreads + 1];
-  __shared__ uint32_t s_n, s_mb;
+  __shared__ uint32_t s_n, s_mb, s_pick, s_pick_below;
+  __shared__ float s_fcut;
+  __shared__ uint32_t s_hist[KS_T];  // 256 bins
+  static_assert(KS_T == 256, "one histogram bin per thread");
   __shared__ int s_box[8];  // lo[3], hi[3], covers, final
   __shared__ R s_q;
   __shared__ KBound s_kb;
@@ -1240,48 +1251,52 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
     }
     return;
   }
+  // set-up on thread 0 (the binary64 pipe is narrow: a division by all 256
+  // threads costs more than the whole gather): the query's record in the
+  // tile's frame, the screen's error bound (from the host's bound for query
+  // offsets up to m_host, else its own), the query's voxel (clamped; any
+  // voxel would do, the walls are measured exactly)
+  int cc[3] = {0, 0, 0};
+  float eq = 0.f;
   if (threadIdx.x == 0) {
     if constexpr (PREC == 1) {
       const float x = __double2float_rn(__dsub_rn(cx[0], T.origin[0]));
       const float y = __double2float_rn(__dsub_rn(cx[1], T.origin[1]));
       const float z = __double2float_rn(__dsub_rn(cx[2], T.origin[2]));
       s_q = make_float4(x, y, z, 0.f);
-      const double m = (double)fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+      const float mf = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
       Thresholds th;
-      knn_thresholds(&th, (double)T.enc_err, ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30);
+      if (mf <= m_host) {
+        th.pad_[0] = alpha_host;
+        eq = eq_host;
+      } else {
+        const double m = (double)mf;
+        const double e_q = ldexp(m, -24) * (1.0 + 1e-6) + ldexp(m, -52) + 1e-30;
+        th.pad_[0] = __double2float_ru(((double)T.enc_err + e_q) * (1.0 + 1e-6));
+        eq = __double2float_ru(e_q);
+      }
       s_kb = make_kbound<1>(th);
+      const float qa[3] = {x, y, z};
+      for (int a = 0; a < nax; ++a) {
+        const float u = floorf(__fmul_rn(__fadd_rn(qa[a], T.D[a]), T.inv_sf[a]));
+        cc[a] = u < 0.f ? 0 : (u > (float)(T.n[a] - 1) ? T.n[a] - 1 : (int)u);
+      }
     } else {
       s_q = make_double4_32a(cx[0], cx[1], cx[2], 0.0);
       Thresholds th;
-      knn_thresholds(&th, 0.0, 0.0);
+      th.pad_[0] = 0.f;
       s_kb = make_kbound<0>(th);
+      for (int a = 0; a < nax; ++a) {
+        double v = floor(__ddiv_rn(__dsub_rn(cx[a], T.lo[a]), T.s[a]));
+        v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
+        cc[a] = (int)v;
+      }
     }
   }
-  // the query's voxel (clamped); binary64 arithmetic runs on thread 0 only
-  // (the binary64 pipe is narrow: a division by all 256 threads costs more
-  // than the whole gather)
-  int cc[3] = {0, 0, 0};
-  if (threadIdx.x == 0)
-    for (int a = 0; a < nax; ++a) {
-      double v = floor(__ddiv_rn(__dsub_rn(cx[a], T.lo[a]), T.s[a]));
-      v = fmin(fmax(v, 0.0), (double)(T.n[a] - 1));
-      cc[a] = (int)v;
-    }
   __syncthreads();
   const R qr = s_q;
   const KBound kb = s_kb;
   const R* __restrict__ pts = PREC == 1 ? reinterpret_cast<const R*>(ix.pts32) : reinterpret_cast<const R*>(ix.pts64s);
-  // block-wide sum of one value per thread (every thread gets it)
-  auto block_sum = [&](uint32_t v) -> uint32_t {
-    v = __reduce_add_sync(0xffffffffu, v);
-    __syncthreads();
-    if (lane == 0) s_red[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-#pragma unroll
-    for (int w = 0; w < KS_T / 32; ++w) t += s_red[w];
-    return t;
-  };
   int Rr = 1;
   bool final_box = false;
   uint32_t mb = 0;
@@ -1289,7 +1304,10 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
     // the box (thread 0): rings around the query's voxel, or the final
     // ball's range
     if (threadIdx.x == 0) {
-      const double rb = final_box ? sqrt(s_d[k - 1]) : 0.0;
+      const double rb = (final_box && PREC == 0) ? sqrt(s_d[k - 1]) : 0.0;
+      // binary32 records: the final ball's range in binary32 with the proven
+      // pad of the voxel coordinates (the k-NN bounded search's formula)
+      const float rbf = (final_box && PREC == 1) ? __fmul_ru(__fsqrt_ru(__double2float_ru(s_d[k - 1])), 1.000001f) : 0.f;
       int cov = 1;
       for (int a = 0; a < 3; ++a) {
         int l0, h0;
@@ -1299,6 +1317,16 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
         } else if (!final_box) {
           l0 = max(cc[a] - Rr, 0);
           h0 = min(cc[a] + Rr, T.n[a] - 1);
+        } else if constexpr (PREC == 1) {
+          const float qv = a == 0 ? s_q.x : (a == 1 ? s_q.y : s_q.z);
+          const float u = __fmul_rn(__fadd_rn(qv, T.D[a]), T.inv_sf[a]);
+          const float rr = __fmul_ru(__fmul_ru(rbf, T.inv_sf[a]), 1.0000005f);
+          float pad = __fadd_ru(__fadd_ru(rr, T.eta), __fmul_ru(__fadd_ru(fabsf(u), fabsf(qv) * T.inv_sf[a]), 3.0e-7f));
+          pad = __fadd_ru(pad, __fmul_ru(eq, T.inv_sf[a]));
+          const float ul = fminf(fmaxf(__fsub_rd(u, pad), -1.0e9f), 1.0e9f);
+          const float uh = fminf(fmaxf(__fadd_ru(u, pad), -1.0e9f), 1.0e9f);
+          l0 = min(max((int)floorf(ul), 0), T.n[a] - 1);
+          h0 = max(min((int)floorf(uh), T.n[a] - 1), 0);
         } else {
           const double l = floor(__ddiv_rn(__dsub_rn(__dsub_rn(cx[a], rb), T.lo[a]), T.s[a])) - 1.0;
           const double h = floor(__ddiv_rn(__dsub_rn(__dadd_rn(cx[a], rb), T.lo[a]), T.s[a])) + 1.0;
@@ -1311,11 +1339,20 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
       }
       s_box[6] = cov;
       s_n = 0;
+      if (final_box) {
+        const float kf = __double2float_ru(s_d[k - 1]);
+        s_fcut = __fadd_ru(kf, 2.0f * kb.at(kf));
+      } else {
+        s_fcut = INFINITY;
+      }
     }
     __syncthreads();  // also: every thread has read s_d before the band is rebuilt
     const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
     const bool covers = s_box[6] != 0;
-    // gather: every point of the box, its screen value and id
+    // gather: every point of the box, its screen value and id (the final
+    // box keeps only the points whose screen value may lie within the
+    // k-th value found so far, kth: the true k nearest are among them)
+    const float fcut = s_fcut;
     for_each_in_box(ix, T, lo, hi, s_start, s_off, [&](uint32_t t, bool valid) {
       float df = 0.f;
       uint32_t id = 0;
@@ -1323,6 +1360,7 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
         const R rec = pts[t];
         df = kd2f(rec, qr);
         id = krec_id(rec);
+        valid = df <= fcut;
       }
       const unsigned bm = __ballot_sync(0xffffffffu, valid);
       uint32_t base = 0;
@@ -1340,17 +1378,48 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
       if (++Rr > KS_MAX_RING) break;
       continue;
     }
-    // the k-th smallest screen value (every value when fewer than k)
+    // an upper bound tau of the k-th smallest screen value, within 2^-8 of
+    // it: two 256-bin histograms of the values' bit patterns (non-negative
+    // binary32 values order as their bits), bits 30..23, then 22..15 of the
+    // bin that holds the k-th; tau = the top of that second bin
     const uint32_t kk = min((uint32_t)k, n);
-    uint32_t klo = 0u, khi = 0x7f800000u;
-    while (kk > 0 && klo < khi) {
-      const uint32_t mid = klo + ((khi - klo) >> 1);
-      uint32_t cnt = 0;
-      for (uint32_t i = threadIdx.x; i < n; i += KS_T) cnt += __float_as_uint(s_f[i]) <= mid ? 1u : 0u;
-      if (block_sum(cnt) >= kk) khi = mid;
-      else klo = mid + 1u;
+    float tau = 0.f;
+    if (kk > 0 && kk == (uint32_t)k) {
+      uint32_t below = 0, prefix = 0;
+      for (int level = 0; level < 2; ++level) {
+        const int shift = level == 0 ? 23 : 15;
+        s_hist[threadIdx.x] = 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += KS_T) {
+          const uint32_t b = __float_as_uint(s_f[i]);
+          if (level == 0 || (b >> 23) == prefix) atomicAdd(&s_hist[(b >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        // inclusive scan of the 256 bins (one per thread)
+        const uint32_t h = s_hist[threadIdx.x];
+        uint32_t inc = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= (uint32_t)o) inc += y;
+        }
+        if (lane == 31) s_red[warp] = inc;
+        __syncthreads();
+        uint32_t wb = 0;
+        for (uint32_t w2 = 0; w2 < warp; ++w2) wb += s_red[w2];
+        inc += wb + below;
+        if (inc >= kk && inc - h < kk) s_pick = threadIdx.x;  // the bin holding the k-th
+        __syncthreads();
+        const uint32_t pick = s_pick;
+        // the count below the picked bin, from its own thread
+        if (threadIdx.x == pick) s_pick_below = inc - h;
+        __syncthreads();
+        below = s_pick_below;
+        prefix = level == 0 ? pick : (prefix << 8) | pick;
+        __syncthreads();  // s_hist, s_red and s_pick are reused
+      }
+      tau = (prefix >> 8) == 255u ? INFINITY : __uint_as_float((prefix << 15) | 0x7fffu);
     }
-    const float tau = __uint_as_float(klo);
     const float bcut = kk < (uint32_t)k ? INFINITY : __fadd_ru(tau, 2.0f * kb.at(tau));
     if (threadIdx.x == 0) s_mb = 0;
     __syncthreads();
@@ -1417,8 +1486,9 @@ __global__ void __launch_bounds__(KS_T) knn_small_kernel(IndexView ix, const dou
     }
     final_box = true;
   }
-  // not decided here: the step-by-step kernel takes the query
-  if (threadIdx.x == 0) over_list[atomicAdd(over_n, 1u)] = e;
+  // not decided here (a box or band too large for shared memory): the
+  // block's first warp runs Algorithm 2 step by step for the query
+  if (warp == 0) knn_grow_one<PREC>(ix, q, e, k, 1, out_idx, out_d2, nullptr, status);
   return;
 out:
   for (int i = (int)threadIdx.x; i < k; i += KS_T) {
@@ -1496,27 +1566,30 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   // cannot decide (boxes or bands too large for its shared memory) run
   // Algorithm 2 step by step with the density rule (the same result)
   if (!all_points && nq > 0 && nq <= kSmallBatch && ix->ntiles == 1) {
-    DevBufs tmp;
-    uint32_t* over = (uint32_t*)tmp.get(4 * (size_t)nq + 64, st);
-    if (!over) return fail(CG_ERR_OOM, "device allocation failed (small k-NN)");
-    uint32_t* over_n = over + nq;
-    cudaError_t e = cudaMemsetAsync(over_n, 0, 4, st);
-    if (e == cudaSuccess) {
+    // the screen's bound for query offsets up to the tile's extent plus
+    // 64 cells (farther queries make their own)
+    const Tile& T0 = ix->tiles_host[0];
+    double mh = 0.0;
+    for (int a = 0; a < 3; ++a)
+      mh = std::max(mh, std::max(std::fabs(T0.lo[a] - T0.origin[a]), std::fabs(T0.hi[a] - T0.origin[a])) + 64.0 * T0.s[a]);
+    const float m_host = (float)mh;
+    const double mq = (double)m_host;
+    const double eqh = std::ldexp(mq, -24) * (1.0 + 1e-6) + std::ldexp(mq, -52) + 1e-30;
+    const float alpha_host = f_up(((double)T0.enc_err + eqh) * (1.0 + 1e-6));
+    const float eq_host = f_up(eqh);
+    {
       ProfScope prof("knn_small", st);
       if (ix->precision == CG_FP32_OFFSET)
-        knn_small_kernel<1><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, over, over_n, C.status);
+        knn_small_kernel<1><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, C.status, m_host,
+                                                      alpha_host, eq_host);
       else
-        knn_small_kernel<0><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, over, over_n, C.status);
+        knn_small_kernel<0><<<(int)nq, KS_T, 0, st>>>(ix->view(), q, (uint32_t)nq, k, idx, d2, C.status, m_host,
+                                                      alpha_host, eq_host);
       note_launch();
-      e = cudaGetLastError();
     }
-    if (e != cudaSuccess) {
-      tmp.release(st);
-      return cuda_fail(e, "small k-NN kernel");
-    }
-    cg_status s = knn_grow_pass(ix, q, nq, k, 1, idx, d2, nullptr, st, C.status, over, over_n);
-    tmp.release(st);
-    return s;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "small k-NN kernel");
+    return CG_OK;
   }
   if (!all_points) {
     cg_status s = prepare_queries(ix, C, q, nq, false, st);

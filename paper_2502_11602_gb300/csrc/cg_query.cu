@@ -737,25 +737,48 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
         R.small_counts = (uint32_t*)R.small_bufs.get(4 * (size_t)kSmallBatch, st);
         R.small_stats = (uint32_t*)R.small_bufs.get(64, st);
         R.small_rows = (int32_t*)R.small_bufs.get(4 * (size_t)kSmallRowCap * (size_t)kSmallBatch, st);
-        if (!R.small_counts || !R.small_stats || !R.small_rows) {
+        if (!R.small_counts || !R.small_stats || !R.small_rows ||
+            cudaMemsetAsync(R.small_stats, 0, 64, st) != cudaSuccess) {  // [8]: the count's finish counter
           R.small_bufs.release(st);
           R.small_counts = R.small_stats = nullptr;
           R.small_rows = nullptr;
           return fail(CG_ERR_OOM, "device allocation failed (small radius pass)");
         }
       }
+      if (!R.small_host) {
+        void* hp = nullptr;
+        void* dp = nullptr;
+        if (cudaHostAlloc(&hp, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(CG_ERR_OOM, "pinned host allocation failed (small radius pass)");
+        }
+        if (cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) {
+          cudaGetLastError();
+          cudaFreeHost(hp);
+          return fail(CG_ERR_CUDA, "mapped host pointer (small radius pass)");
+        }
+        R.small_host = (unsigned long long*)hp;
+        R.small_host_dev = (unsigned long long*)dp;
+      }
       uint32_t* counts = R.small_counts;
       uint32_t* stats = R.small_stats;
       int32_t* rows = R.small_rows;
-      cudaError_t e =
-          launch_small_count(ix->view(), kernel, q, (uint32_t)nq, r, counts, rows, offsets, stats, C.status, st);
-      uint32_t maxrow = 0, w = 0;
-      HostRead rd;
-      rd.get(total_host, offsets + nq, 8);
-      rd.get(&maxrow, stats, 4);
-      rd.get(&w, C.status, 4);
-      if (e == cudaSuccess) e = rd.sync(st);
+      // a search-into call: small results are copied by the count itself,
+      // larger ones by a copy kernel issued before the one sync
+      cudaError_t e = launch_small_count(ix->view(), ix->tiles_host[0], kernel, q, (uint32_t)nq, r, counts, rows,
+                                         offsets, stats, C.status, R.small_host_dev, R.direct_out, R.direct_cap, st);
+      R.direct_done = false;
+      bool copy_kernel = false;
+      if (e == cudaSuccess && R.direct_out && (R.direct_cap > kSmallDirectMax || (uint32_t)nq > kSmallDirectQueries)) {
+        e = launch_small_fill(rows, (uint32_t)nq, offsets, R.direct_out, C.status, st, R.direct_cap, stats + 9);
+        copy_kernel = e == cudaSuccess;
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_fail(e, "small radius count");
+      *total_host = (int64_t)((volatile unsigned long long*)R.small_host)[0];
+      const uint32_t maxrow = (uint32_t)((volatile unsigned long long*)R.small_host)[1];
+      const uint32_t w = (uint32_t)((volatile unsigned long long*)R.small_host)[2];
+      R.direct_done = copy_kernel || ((volatile unsigned long long*)R.small_host)[3] != 0ull;
       cg_status s = status_verdict(w, C.status, st);
       if (s != CG_OK) return s;
       if (maxrow <= (uint32_t)kSmallRowCap) {
@@ -1025,6 +1048,24 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
 cg_status radius_pass(cg_index* ix, bool all_points, const double* q, int64_t nq, double r, int kernel,
                       bool fill, int64_t* offsets, int32_t* out, int64_t* total_host, cudaStream_t st) {
   return radius_pass(ix, ix->ctx, all_points, q, nq, r, kernel, fill, offsets, out, total_host, st);
+}
+
+cg_status radius_search_into(cg_index* ix, QueryCtx& C, const double* q, int64_t nq, double r, int kernel,
+                             int64_t* offsets, int32_t* out, int64_t cap, int64_t* total_host, cudaStream_t st) {
+  RadiusState& R = C.radius;
+  R.direct_out = cap > 0 ? out : nullptr;
+  R.direct_cap = cap;
+  R.direct_done = false;
+  int64_t total = 0;
+  cg_status s = radius_pass(ix, C, false, q, nq, r, kernel, false, offsets, nullptr, &total, st);
+  const bool copied = R.small && R.direct_done;
+  R.direct_out = nullptr;
+  R.direct_done = false;
+  if (s != CG_OK) return s;
+  *total_host = total;
+  if (total > cap) return fail(CG_ERR_OVERFLOW, "the rows exceed the output capacity (the count stands)");
+  if (copied) return CG_OK;  // the small count has written the rows
+  return radius_pass(ix, C, false, q, nq, r, kernel, true, offsets, out, nullptr, st);
 }
 
 // ------------------------------------------------- replayed (graph) pass

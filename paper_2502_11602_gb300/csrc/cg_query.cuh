@@ -189,11 +189,16 @@ inline bool zw_applies(const cg_index* ix, int kern) {
 // to a scratch buffer of kSmallRowCap entries per query; the fill copies).
 constexpr int64_t kSmallBatch = 1024;
 constexpr int kSmallRowCap = 2048;
-cudaError_t launch_small_count(const IndexView& iv, int kern, const double* q, uint32_t nq, double r,
+// results the small count's last block copies itself (larger ones: a copy
+// kernel, one block per query)
+constexpr int64_t kSmallDirectMax = 4096;
+constexpr uint32_t kSmallDirectQueries = 32;
+cudaError_t launch_small_count(const IndexView& iv, const Tile& T, int kern, const double* q, uint32_t nq, double r,
                                uint32_t* counts, int32_t* rows, int64_t* offsets, uint32_t* stats,
-                               uint32_t* status, cudaStream_t st);
+                               uint32_t* status, unsigned long long* host_out, int32_t* direct_out,
+                               int64_t direct_cap, cudaStream_t st);
 cudaError_t launch_small_fill(const int32_t* rows, uint32_t nq, const int64_t* offsets, int32_t* out,
-                              uint32_t* status, cudaStream_t st);
+                              uint32_t* status, cudaStream_t st, int64_t cap = -1, const uint32_t* skip = nullptr);
 
 QuerySet query_set(cg_index* ix, const double* q, int64_t nq, bool all_points);
 

@@ -94,3 +94,32 @@ def test_small_knn_batches(prec, dim):
                 assert np.array_equal(d2.cpu().numpy(), r_d2), (m, k)
     finally:
         ix.close()
+
+
+def test_search_into_capacity_and_overflow():
+    # cg_radius_search_into: rows that fit are written by the one call; a
+    # buffer that is too small gives CG_ERR_OVERFLOW with the total, and the
+    # count stands for a fill into a buffer of that size
+    xyz = cloudgen.als_uniform(50_000, extent=(60.0, 60.0), seed=8)
+    ref = oracle.Index(xyz, 1.0)
+    ix = cg.Index(torch.from_numpy(xyz).to(DEV), 1.0)
+    try:
+        for m in (1, 300, 3000):  # the last one beyond the small path
+            q = _queries(xyz, m, seed=70 + m)
+            qd = torch.from_numpy(q).to(DEV)
+            o_off, o_ind = ref.radius_search(q, 1.0, threads=8)
+            off = torch.empty(m + 1, dtype=torch.int64, device=DEV)
+            big = torch.full((int(o_off[-1]) + 10,), -1, dtype=torch.int32, device=DEV)
+            fits, total = cg.cg_radius_search_into(ix.h, qd, 1.0, cg.SPHERE, off, big, big.numel())
+            assert fits and total == int(o_off[-1])
+            assert np.array_equal(off.cpu().numpy(), o_off)
+            assert np.array_equal(big[:total].cpu().numpy(), o_ind)
+            small = torch.empty(max(total // 2, 1), dtype=torch.int32, device=DEV)
+            fits, total2 = cg.cg_radius_search_into(ix.h, qd, 1.0, cg.SPHERE, off, small, small.numel())
+            assert not fits and total2 == total
+            out = torch.empty(total, dtype=torch.int32, device=DEV)
+            cg.cg_radius_fill(ix.h, qd, 1.0, cg.SPHERE, off, out)
+            cg.cg_index_status(ix.h)
+            assert np.array_equal(out.cpu().numpy(), o_ind)
+    finally:
+        ix.close()
