@@ -89,9 +89,6 @@ struct RadiusState {
   DevBufs small_bufs;
   uint32_t *small_counts = nullptr, *small_stats = nullptr;
   int32_t* small_rows = nullptr;
-  // mapped pinned words the small count writes for the host (total, largest
-  // row, status word): read after a stream sync, no copy launch
-  unsigned long long *small_host = nullptr, *small_host_dev = nullptr;
   // search-into calls: the small count also copies the rows into the
   // caller's buffer (when they fit its capacity) before its one sync
   int32_t* direct_out = nullptr;
@@ -111,10 +108,6 @@ struct QueryCtx {
     plan.bufs.release(st);
     radius.bufs.release(st);
     radius.small_bufs.release(st);
-    if (radius.small_host) {
-      cudaStreamSynchronize(st);
-      cudaFreeHost(radius.small_host);
-    }
     plan = QueryPlan();
     radius = RadiusState();
   }

@@ -716,6 +716,18 @@ cg_status make_zchunks(cg_index* ix, float dz, uint32_t qmax, DevBufs& bufs, uin
   return CG_OK;
 }
 
+// Mapped pinned words the small count writes for the host (total, longest
+// row, status word, rows copied): one block per host thread, used between a
+// count's launch and its stream sync in the same call.
+struct SmallHostBlock {
+  unsigned long long* h = nullptr;  // host address
+  unsigned long long* d = nullptr;  // the same words as the device addresses them
+  ~SmallHostBlock() {
+    if (h) cudaFreeHost(h);
+  }
+};
+thread_local SmallHostBlock t_small_host;
+
 // Radius pass state kept on the index between the count and fill calls.
 cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, double r,
                       int kernel, bool fill, int64_t* offsets, int32_t* out, int64_t* total_host,
@@ -745,7 +757,7 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
           return fail(CG_ERR_OOM, "device allocation failed (small radius pass)");
         }
       }
-      if (!R.small_host) {
+      if (!t_small_host.h) {
         void* hp = nullptr;
         void* dp = nullptr;
         if (cudaHostAlloc(&hp, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
@@ -757,16 +769,17 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
           cudaFreeHost(hp);
           return fail(CG_ERR_CUDA, "mapped host pointer (small radius pass)");
         }
-        R.small_host = (unsigned long long*)hp;
-        R.small_host_dev = (unsigned long long*)dp;
+        t_small_host.h = (unsigned long long*)hp;
+        t_small_host.d = (unsigned long long*)dp;
       }
+      volatile unsigned long long* hw = t_small_host.h;
       uint32_t* counts = R.small_counts;
       uint32_t* stats = R.small_stats;
       int32_t* rows = R.small_rows;
       // a search-into call: small results are copied by the count itself,
       // larger ones by a copy kernel issued before the one sync
       cudaError_t e = launch_small_count(ix->view(), ix->tiles_host[0], kernel, q, (uint32_t)nq, r, counts, rows,
-                                         offsets, stats, C.status, R.small_host_dev, R.direct_out, R.direct_cap, st);
+                                         offsets, stats, C.status, t_small_host.d, R.direct_out, R.direct_cap, st);
       R.direct_done = false;
       bool copy_kernel = false;
       if (e == cudaSuccess && R.direct_out && (R.direct_cap > kSmallDirectMax || (uint32_t)nq > kSmallDirectQueries)) {
@@ -775,10 +788,10 @@ cg_status radius_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* 
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return cuda_fail(e, "small radius count");
-      *total_host = (int64_t)((volatile unsigned long long*)R.small_host)[0];
-      const uint32_t maxrow = (uint32_t)((volatile unsigned long long*)R.small_host)[1];
-      const uint32_t w = (uint32_t)((volatile unsigned long long*)R.small_host)[2];
-      R.direct_done = copy_kernel || ((volatile unsigned long long*)R.small_host)[3] != 0ull;
+      *total_host = (int64_t)hw[0];
+      const uint32_t maxrow = (uint32_t)hw[1];
+      const uint32_t w = (uint32_t)hw[2];
+      R.direct_done = copy_kernel || hw[3] != 0ull;
       cg_status s = status_verdict(w, C.status, st);
       if (s != CG_OK) return s;
       if (maxrow <= (uint32_t)kSmallRowCap) {
