@@ -293,8 +293,9 @@ def _alg_tests(xyz, r: float, cell: float) -> int:
 OPS_PER_TEST = 7
 # sources of the kernels whose DRAM traffic profiles/traffic_radius_als12m.txt records
 TRAFFIC_SRC = ["cg_radius2.cu", "cg_f32x2.cuh", "cg_query.cu", "cg_query.cuh", "cg_internal.cuh", "cg_zwin.cu"]
-COUNT_PHASES = ("radius_count5_1k", "radius_count5_2k", "radius_count2", "radius_v1_count")
-FILL_PHASES = ("radius_fill5_1k", "radius_fill5_2k", "radius_fill2", "radius_v1_fill", "radius_row_sort")
+COUNT_PHASES = ("radius_count5_512", "radius_count5_1k", "radius_count5_2k", "radius_count2", "radius_v1_count")
+FILL_PHASES = ("radius_fill5_512", "radius_fill5_1k", "radius_fill5_2k", "radius_fill2", "radius_v1_fill",
+               "radius_row_sort")
 
 
 def run_ours(args):
