@@ -357,16 +357,38 @@ __global__ void __launch_bounds__(KT) knn_fast_kernel(IndexView ix, QuerySet qs,
 // the bounded search with the box's exact k-th value as an upper bound of
 // the true one; groups too large to stage go to the ring-by-ring path.
 constexpr int K5_NB = 64;
-constexpr int K5_Q = 8;  // queued candidates per lane
+constexpr int K5_Q = 12;  // queued candidates per lane
 
 // Shared memory of a slot of gw warps: the group's staged box (records,
 // buckets, spans, a few broadcast words), then one candidate queue per warp.
 template <int KC>
 struct K5Smem {
   static constexpr size_t tables = (16 * (size_t)KC + (size_t)KC + 4 * (2 * K5_NB + 2) + 4 * 2 * 12 + 4 * 4 + 15) / 16 * 16;
-  static constexpr size_t queue = 8 * (size_t)K5_Q * 32;
+  static constexpr size_t queue = 4 * (size_t)K5_Q * 32;
   __host__ __device__ static constexpr size_t per_slot(int gw) { return tables + queue * (size_t)gw; }
 };
+
+// A candidate's binary32 value with its staged slot j (< 2048) in the low 11
+// mantissa bits: the lists and queues then move one word per entry.  The
+// packed value p orders as the value up to a relative 2^-12 (|p - d| <
+// 2^-12 d, plus 2^-138 at d = 0); the band and the stop test below widen by
+// that much.  d is clamped below +inf so that no NaN pattern arises.
+__device__ __forceinline__ float k5_pack(float d, uint32_t j) {
+  return __uint_as_float((__float_as_uint(fminf(d, 3.0e38f)) & ~0x7ffu) | j);
+}
+__device__ __forceinline__ uint32_t k5_slot(float p) { return __float_as_uint(p) & 0x7ffu; }
+
+template <int L>
+__device__ __forceinline__ void topl_insert1(float (&v)[L], float p) {
+  // v ascending: p goes before the first entry it is below; every position
+  // is computed from the old list (no dependent chain of selects)
+  bool c[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) c[i] = p < v[i];
+#pragma unroll
+  for (int i = L - 1; i > 0; --i) v[i] = c[i - 1] ? v[i - 1] : (c[i] ? p : v[i]);
+  v[0] = c[0] ? p : v[0];
+}
 
 // Barrier of the GW warps of one slot (named barrier 1 + slot).
 template <int GW>
@@ -441,8 +463,7 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
   uint32_t* sp_start = cursor + K5_NB + 1;                        // [12]
   uint32_t* sp_off = sp_start + 12;                               // [12]
   uint32_t* sbox = sp_off + 12;                                   // [4]: group, K
-  float* qd = reinterpret_cast<float*>(base + S::tables + S::queue * (size_t)wis);  // [Q][32] queued values
-  uint32_t* qj = reinterpret_cast<uint32_t*>(qd + K5_Q * 32);                       // [Q][32] queued slots
+  float* qd = reinterpret_cast<float*>(base + S::tables + S::queue * (size_t)wis);  // [Q][32] queued packed values
   const Thresholds thr = *thr_p;
   const KBound kb = make_kbound<1>(thr);
   const float4* __restrict__ pts = ix.pts32;
@@ -552,43 +573,35 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
       const float4 q = live ? qsrc[qc + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
       const uint32_t qid = __float_as_uint(q.w);
       const float rq = centre_dist(q, cx, cy, cz, zw);
-      float v[L];
-      uint32_t id[L];
+      float v[L];  // packed values (k5_pack), ascending
 #pragma unroll
-      for (int i = 0; i < L; ++i) { v[i] = INFINITY; id[i] = 0xffffffffu; }
-      float gate = INFINITY;  // the L-th value at the last merge
+      for (int i = 0; i < L; ++i) v[i] = INFINITY;
+      float gate = INFINITY;  // the L-th packed value at the last merge
       uint32_t nqd = 0;       // queued candidates of this lane
       for (int u = 0; u < K5_NB; ++u) {
         const uint32_t s0 = bstart[u], s1 = bstart[u + 1];
         if (s0 == s1) continue;
-        // later candidates p have |p - q| >= t, so d2(p) >= t^2 and their
+        // later candidates p have |p - q| >= t, so d2(p) >= t^2, their
         // binary32 value is at least t^2 - B(t^2) (B grows slower than d2)
+        // and their packed value at least that times 1 - 2^-11
         const float t = __fsub_rd(__fsub_rd((float)u * bw, rq), 1e-3f * bw + 1e-5f);
         const float t2 = __fmul_rd(t, t);
-        const bool done = !live || (t > 0.f && __fsub_rd(t2, kb.at(t2)) > gate);
+        const bool done = !live || (t > 0.f && __fmul_rd(__fsub_rd(t2, kb.at(t2)), 0.99951171875f) > gate);
         if (__all_sync(0xffffffffu, done)) break;
         for (uint32_t j = s0; j < s1; j += 2) {  // two candidates per step
           const bool two = j + 1 < s1;
           const float4 p = recs[j];
           const float4 p1 = recs[two ? j + 1 : j];
           const float dx = __fsub_rn(p.x, q.x), dy = __fsub_rn(p.y, q.y), dz = __fsub_rn(p.z, q.z);
-          const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const float d = k5_pack(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))), j);
           const float ex1 = __fsub_rn(p1.x, q.x), ey1 = __fsub_rn(p1.y, q.y), ez1 = __fsub_rn(p1.z, q.z);
-          const float d1 = __fmaf_rn(ez1, ez1, __fmaf_rn(ey1, ey1, __fmul_rn(ex1, ex1)));
-          if (live && d < gate) {
-            qd[nqd * 32 + lane] = d;
-            qj[nqd * 32 + lane] = j;
-            ++nqd;
-          }
-          if (live && two && d1 < gate) {
-            qd[nqd * 32 + lane] = d1;
-            qj[nqd * 32 + lane] = j + 1;
-            ++nqd;
-          }
+          const float d1 = k5_pack(__fmaf_rn(ez1, ez1, __fmaf_rn(ey1, ey1, __fmul_rn(ex1, ex1))), j + 1);
+          if (live && d < gate) qd[(nqd++) * 32 + lane] = d;
+          if (live && two && d1 < gate) qd[(nqd++) * 32 + lane] = d1;
           if (__any_sync(0xffffffffu, nqd >= (uint32_t)K5_Q - 1u)) {  // merge the queues
             for (uint32_t e = 0; e < nqd; ++e) {
               const float de = qd[e * 32 + lane];
-              if (de < v[L - 1]) topl_insert<L>(v, id, de, qj[e * 32 + lane]);
+              if (de < v[L - 1]) topl_insert1<L>(v, de);
             }
             nqd = 0;
             gate = v[L - 1];
@@ -597,7 +610,7 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
       }
       for (uint32_t e = 0; e < nqd; ++e) {
         const float de = qd[e * 32 + lane];
-        if (de < v[L - 1]) topl_insert<L>(v, id, de, qj[e * 32 + lane]);
+        if (de < v[L - 1]) topl_insert1<L>(v, de);
       }
       if (!live) continue;
       // found: candidates in the list (all of the box when it holds fewer than L)
@@ -617,7 +630,12 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
         float tau = 0.f;  // v is ascending: the k-th value is the largest of the first kk
 #pragma unroll
         for (int i = 0; i < L; ++i) tau = fmaxf(tau, i < kk ? v[i] : 0.f);
-        const float cut = __fadd_ru(tau, 2.0f * kb.at(tau));
+        // k packed values <= tau: their binary32 values are at most
+        // tau / (1 - 2^-12), the exact k-th at most that plus B; every point
+        // with an exact value up to there has a packed value up to
+        // (tau / (1 - 2^-12) + 2 B) (1 + 2^-12) <= cut
+        const float cut = __fadd_ru(__fadd_ru(__fmul_ru(tau, 1.0009765625f), 2.0f * __fmul_ru(kb.at(tau), 1.001f)),
+                                    1.0e-37f);
 #pragma unroll
         for (int i = 0; i < L; ++i) m += v[i] <= cut ? 1 : 0;
         if (m == L && v[L - 1] < INFINITY) undecided = true;  // the band may continue past the list
@@ -631,7 +649,7 @@ __global__ void __launch_bounds__(NWARP * 32) knn5_kernel(IndexView ix, QuerySet
 #pragma unroll
         for (int i = 0; i < L; ++i) {
           if (i < m) {
-            cid[i] = __float_as_uint(recs[id[i]].w);
+            cid[i] = __float_as_uint(recs[k5_slot(v[i])].w);
             ex[i] = exact_d2(ix.xyz64 + 3 * (size_t)cid[i], q64 + 3 * (size_t)qid);
           } else {
             cid[i] = 0xffffffffu;
