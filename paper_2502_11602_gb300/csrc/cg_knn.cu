@@ -1520,7 +1520,7 @@ out:
 
 // Binary32 fast path for k <= 32: group boxes of radius 1 in two size
 // classes (staged boxes of <= 1024 and <= 2048 candidates; list length
-// k + 4 rounded up to 12, 20 or 36), then the bounded search of the queries
+// the class's largest k + 2: 10, 18 or 34), then the bounded search of the queries
 // left undecided.  bslot / br2 have room for every query; ctrs[4..6] are
 // the box launches' group counters, ctrs[9] the bounded list's length,
 // ctrs[0] the ring-by-ring list's.
@@ -1551,17 +1551,17 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
   // warps per group: 1, 2, 4 for the three classes (their groups hold about
   // 1, 2.5 and 4 chunks of 32 queries), sharing the staged box
   if (k <= 8) {
-    CG_K5(512, 12, 4, 1, 0u);
-    CG_K5(1024, 12, 4, 2, 1u);
-    CG_K5(2048, 12, 4, 4, 2u);
+    CG_K5(512, 10, 4, 1, 0u);
+    CG_K5(1024, 10, 4, 2, 1u);
+    CG_K5(2048, 10, 4, 4, 2u);
   } else if (k <= 16) {
-    CG_K5(512, 20, 4, 1, 0u);
-    CG_K5(1024, 20, 4, 2, 1u);
-    CG_K5(2048, 20, 4, 4, 2u);
+    CG_K5(512, 18, 4, 1, 0u);
+    CG_K5(1024, 18, 4, 2, 1u);
+    CG_K5(2048, 18, 4, 4, 2u);
   } else {
-    CG_K5(512, 36, 4, 1, 0u);
-    CG_K5(1024, 36, 4, 2, 1u);
-    CG_K5(2048, 36, 4, 4, 2u);
+    CG_K5(512, 34, 4, 1, 0u);
+    CG_K5(1024, 34, 4, 2, 1u);
+    CG_K5(2048, 34, 4, 4, 2u);
   }
 #undef CG_K5
   f.join();
