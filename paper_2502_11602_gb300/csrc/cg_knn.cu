@@ -731,10 +731,13 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
   __shared__ uint32_t s_id[KB_WARPS][KB_CAP];
   __shared__ uint32_t s_bid[KB_WARPS][KB_CAP / 2];
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  __shared__ uint32_t s_zst[KB_WARPS][64], s_zoff[KB_WARPS][64];  // height-cut column spans
   double* wd2 = s_d2[warp];
   float* wf = s_f[warp];
   uint32_t* wid = s_id[warp];
   uint32_t* bid = s_bid[warp];
+  uint32_t* zst = s_zst[warp];
+  uint32_t* zoff = s_zoff[warp];
   const Thresholds thr = *thr_p;
   const KBound kb = make_kbound<1>(thr);
   const float4* __restrict__ pts = ix.pts32;
@@ -769,7 +772,98 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
     const float cut = __fadd_ru(r2u, 2.0f * kb.at(r2u));
     uint32_t m = 0;
     const int ni = hi[0] - lo[0] + 1, nj = hi[1] - lo[1] + 1;
-    const int ncol = (ni > 0 && nj > 0) ? (dim == 2 ? ni : ni * nj) : 0;
+    // 2D grids with height-sorted columns: every voxel column of the box cut
+    // to the candidate test's height range.  A record passes the test only
+    // if RN(dz^2) <= cut (dz = RN(z~_p - z~_q)), so |z~_p - z~_q| <=
+    // sqrt(cut) (1 + 2^-23); the window takes 1 + 1e-6.  The columns' spans
+    // are found lane-parallel (a bisection per column), then all lanes walk
+    // the concatenation.
+    const bool zcut = dim == 2 && ix.pts32z != nullptr && ni > 0 && nj > 0 && ni * nj <= 64;
+    if (zcut) {
+      const float4* __restrict__ zs = ix.pts32z;
+      const int nc = ni * nj;
+      const float zh = __fmul_ru(__fsqrt_ru(cut), 1.000001f);
+      const float zlo = __fsub_rd(q.z, zh), zhi = __fadd_ru(q.z, zh);
+      uint32_t st2[2] = {0u, 0u}, ln2[2] = {0u, 0u};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = (int)lane + 32 * h;
+        if (c < nc) {
+          const uint32_t key = T.key_base + (uint32_t)(lo[0] + c / nj) * (uint32_t)T.n[1] + (uint32_t)(lo[1] + c % nj);
+          uint2 sp = voxel_span(ix, T, key);
+          if (sp.y - sp.x > 1u && sp.y - sp.x <= kZsortMax) {  // a height-sorted run
+            uint32_t a = sp.x, b = sp.y;  // first height >= zlo
+            while (a < b) {
+              const uint32_t mid = (a + b) >> 1;
+              if (__ldg(&zs[mid].z) < zlo) a = mid + 1;
+              else b = mid;
+            }
+            uint32_t d = a, f = sp.y;  // first height > zhi
+            while (d < f) {
+              const uint32_t mid = (d + f) >> 1;
+              if (__ldg(&zs[mid].z) <= zhi) d = mid + 1;
+              else f = mid;
+            }
+            sp = make_uint2(a, d);
+          }
+          st2[h] = sp.x;
+          ln2[h] = sp.y - sp.x;
+        }
+      }
+      // offsets of the columns in the order c = 0 .. nc - 1
+      uint32_t base = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t incl = ln2[h];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= (uint32_t)o) incl += y;
+        }
+        const int c = (int)lane + 32 * h;
+        if (c < nc) {
+          zst[c] = st2[h];
+          zoff[c] = base + incl - ln2[h];
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      const uint32_t total = base;
+      __syncwarp();
+      for (uint32_t i0 = 0; i0 < total; i0 += 128) {  // four loads in flight per lane
+        float4 p[4];
+        bool pick[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t i = i0 + 32u * u + lane;
+          pick[u] = i < total;
+          p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (pick[u]) {
+            int a = 0, b = nc - 1;  // the column holding candidate i
+            while (a < b) {
+              const int mid = (a + b + 1) >> 1;
+              if (zoff[mid] <= i) a = mid;
+              else b = mid - 1;
+            }
+            p[u] = __ldg(zs + zst[a] + (i - zoff[a]));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float dx = __fsub_rn(p[u].x, q.x), dy = __fsub_rn(p[u].y, q.y), dz = __fsub_rn(p[u].z, q.z);
+          const float dv = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          pick[u] = pick[u] && dv <= cut;
+          const unsigned bm = __ballot_sync(0xffffffffu, pick[u]);
+          const uint32_t pos = m + __popc(bm & lanemask_lt());
+          if (pick[u] && pos < (uint32_t)KB_CAP) {
+            wid[pos] = __float_as_uint(p[u].w);
+            wf[pos] = dv;
+          }
+          m += __popc(bm);
+        }
+      }
+      __syncwarp();
+    }
+    const int ncol = (zcut || ni <= 0 || nj <= 0) ? 0 : (dim == 2 ? ni : ni * nj);
     for (int cidx = 0; cidx < ncol; ++cidx) {
       uint32_t k0, k1;
       if (dim == 2) {
