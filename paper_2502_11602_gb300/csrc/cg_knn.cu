@@ -1612,9 +1612,9 @@ out:
 
 }  // namespace
 
-// Binary32 fast path for k <= 32: group boxes of radius 1 in two size
-// classes (staged boxes of <= 1024 and <= 2048 candidates; list length
-// the class's largest k + 2: 10, 18 or 34), then the bounded search of the queries
+// Binary32 fast path (k <= 64): group boxes of radius 1 in three size
+// classes (staged boxes of <= 512, 1024 and 2048 candidates; list length
+// the class's largest k + 2: 10, 18, 34 or 66), then the bounded search of the queries
 // left undecided.  bslot / br2 have room for every query; ctrs[4..6] are
 // the box launches' group counters, ctrs[9] the bounded list's length,
 // ctrs[0] the ring-by-ring list's.
@@ -1652,10 +1652,14 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
     CG_K5(512, 18, 4, 1, 0u);
     CG_K5(1024, 18, 4, 2, 1u);
     CG_K5(2048, 18, 4, 4, 2u);
-  } else {
+  } else if (k <= 32) {
     CG_K5(512, 34, 4, 1, 0u);
     CG_K5(1024, 34, 4, 2, 1u);
     CG_K5(2048, 34, 4, 4, 2u);
+  } else {
+    CG_K5(512, 66, 4, 1, 0u);
+    CG_K5(1024, 66, 4, 2, 1u);
+    CG_K5(2048, 66, 4, 4, 2u);
   }
 #undef CG_K5
   f.join();
@@ -1752,22 +1756,8 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const IndexView iv = ix->view();
-  if (ix->precision == CG_FP32_OFFSET && k <= 32) {
+  if (ix->precision == CG_FP32_OFFSET && k <= 64) {
     e = launch_knn5(iv, qs, thr, k, idx, d2, slow, bslot, br2, ctrs, C.status, st);
-    {
-      ProfScope prof("knn_slow", st);
-      knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2);
-    }
-    note_launch();
-  } else if (ix->precision == CG_FP32_OFFSET) {
-    const size_t smem = knn_smem<1>();
-    cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    {
-      ProfScope prof("knn_fast", st);
-      knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, thr, k, idx, d2, slow, ctrs, ctrs + 4, C.status);
-    }
-    note_launch();
     {
       ProfScope prof("knn_slow", st);
       knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, slow, ctrs, idx, d2);
@@ -1862,15 +1852,8 @@ cg_status knn_replay(cg_index* ix, KnnWork& w, const uint32_t* nkeys_dev, uint32
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const IndexView iv = ix->view();
-  if (ix->precision == CG_FP32_OFFSET && k <= 32) {
+  if (ix->precision == CG_FP32_OFFSET && k <= 64) {
     e = launch_knn5(iv, qs, w.thr, k, idx, d2, w.slow, w.bslot, w.br2, w.ctrs, ix->status, st);
-    knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, w.slow, w.ctrs, idx, d2); note_launch();
-  } else if (ix->precision == CG_FP32_OFFSET) {
-    const size_t smem = knn_smem<1>();
-    cudaFuncSetAttribute(knn_fast_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per = (int)std::max<size_t>(1, std::min<size_t>(8, (227 * 1024) / (smem + 1024)));
-    knn_fast_kernel<1><<<sms * per, KT, smem, st>>>(iv, qs, w.thr, k, idx, d2, w.slow, w.ctrs, w.ctrs + 4,
-                                                     ix->status); note_launch();
     knn_slow_kernel<1><<<sms * 8, 128, 0, st>>>(iv, qs, k, w.slow, w.ctrs, idx, d2); note_launch();
   } else {
     const size_t smem = knn_smem<0>();
