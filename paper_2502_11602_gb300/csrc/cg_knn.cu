@@ -792,19 +792,23 @@ __global__ void __launch_bounds__(KB_WARPS * 32, 7) knn_bounded_kernel(IndexView
           const uint32_t key = T.key_base + (uint32_t)(lo[0] + c / nj) * (uint32_t)T.n[1] + (uint32_t)(lo[1] + c % nj);
           uint2 sp = voxel_span(ix, T, key);
           if (sp.y - sp.x > 1u && sp.y - sp.x <= kZsortMax) {  // a height-sorted run
-            uint32_t a = sp.x, b = sp.y;  // first height >= zlo
-            while (a < b) {
-              const uint32_t mid = (a + b) >> 1;
-              if (__ldg(&zs[mid].z) < zlo) a = mid + 1;
-              else b = mid;
+            // first height >= zlo (a), first height > zhi (d); the two
+            // bisections step together, so their loads overlap
+            uint32_t a = sp.x, b = sp.y, d = sp.x, f = sp.y;
+            while (a < b || d < f) {
+              const uint32_t m1 = (a + b) >> 1, m2 = (d + f) >> 1;
+              const float z1 = a < b ? __ldg(&zs[m1].z) : 0.f;
+              const float z2 = d < f ? __ldg(&zs[m2].z) : 0.f;
+              if (a < b) {
+                if (z1 < zlo) a = m1 + 1;
+                else b = m1;
+              }
+              if (d < f) {
+                if (z2 <= zhi) d = m2 + 1;
+                else f = m2;
+              }
             }
-            uint32_t d = a, f = sp.y;  // first height > zhi
-            while (d < f) {
-              const uint32_t mid = (d + f) >> 1;
-              if (__ldg(&zs[mid].z) <= zhi) d = mid + 1;
-              else f = mid;
-            }
-            sp = make_uint2(a, d);
+            sp = make_uint2(a, d > a ? d : a);
           }
           st2[h] = sp.x;
           ln2[h] = sp.y - sp.x;

@@ -156,20 +156,24 @@ __global__ void __launch_bounds__(PT) radius_plan_kernel(IndexView ix, QuerySet 
       start = sp.x;
       len = sp.y - sp.x;
       if (PREC == 1 && zw && len > 0 && len <= kZsortMax) {
-        uint32_t a = 0, c = len;  // first height >= zlo
-        while (a < c) {
-          const uint32_t m = (a + c) >> 1;
-          if ((float)pts[start + m].z < zlo) a = m + 1;
-          else c = m;
-        }
-        uint32_t d = a, f = len;  // first height > zhi
-        while (d < f) {
-          const uint32_t m = (d + f) >> 1;
-          if ((float)pts[start + m].z <= zhi) d = m + 1;
-          else f = m;
+        // the first height >= zlo (a) and the first height > zhi (d): the two
+        // bisections step together, so their loads overlap
+        uint32_t a = 0, c = len, d = 0, f = len;
+        while (a < c || d < f) {
+          const uint32_t m1 = (a + c) >> 1, m2 = (d + f) >> 1;
+          const float z1 = a < c ? (float)pts[start + m1].z : 0.f;
+          const float z2 = d < f ? (float)pts[start + m2].z : 0.f;
+          if (a < c) {
+            if (z1 < zlo) a = m1 + 1;
+            else c = m1;
+          }
+          if (d < f) {
+            if (z2 <= zhi) d = m2 + 1;
+            else f = m2;
+          }
         }
         start += a;
-        len = d - a;
+        len = d > a ? d - a : 0u;
       }
     }
     const unsigned nonempty = __ballot_sync(0xffffffffu, len > 0);
