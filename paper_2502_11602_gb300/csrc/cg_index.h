@@ -231,11 +231,9 @@ cg_status radius_search_into(cg_index* ix, QueryCtx& C, const double* q, int64_t
 cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, int64_t nq, int k, int32_t* idx,
                    double* d2, cudaStream_t st);
 // Algorithm 2 step by step under a growth policy (0 monotone, 1 density),
-// with the voxels each search visited (cg_knn.cu); with a list, only the
-// queries it names (its length on the device).
+// with the voxels each search visited (cg_knn.cu).
 cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
-                        int64_t* visited, cudaStream_t st, uint32_t* status = nullptr,
-                        const uint32_t* list = nullptr, const uint32_t* list_n = nullptr);
+                        int64_t* visited, cudaStream_t st, uint32_t* status = nullptr);
 cg_status build_work_alloc(cg_index* ix, BuildWork& w, cudaStream_t st);
 cg_status build_replay(cg_index* ix, BuildWork& w, const double* xyz, cudaStream_t st);
 cg_status radius_work_alloc(cg_index* ix, RadiusWork& w, uint32_t cap_nb, double headroom, int64_t total,

@@ -1273,13 +1273,9 @@ template <int PREC>
 __global__ void __launch_bounds__(128) knn_grow_kernel(IndexView ix, const double* __restrict__ q, uint32_t nq,
                                                        int k, int policy, int32_t* __restrict__ out_idx,
                                                        double* __restrict__ out_d2,
-                                                       long long* __restrict__ visited, uint32_t* status,
-                                                       const uint32_t* __restrict__ list, const uint32_t* list_n) {
-  // every query, or the queries of a list (those another kernel left)
-  const uint32_t nrun = list ? min(*list_n, nq) : nq;
-  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nrun;
-       w += gridDim.x * (blockDim.x / 32))
-    knn_grow_one<PREC>(ix, q, list ? list[w] : w, k, policy, out_idx, out_d2, visited, status);
+                                                       long long* __restrict__ visited, uint32_t* status) {
+  for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < nq; w += gridDim.x * (blockDim.x / 32))
+    knn_grow_one<PREC>(ix, q, w, k, policy, out_idx, out_d2, visited, status);
 }
 
 template <int PREC>
@@ -1790,8 +1786,7 @@ cg_status knn_pass(cg_index* ix, QueryCtx& C, bool all_points, const double* q, 
 
 
 cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int policy, int32_t* idx, double* d2,
-                        int64_t* visited, cudaStream_t st, uint32_t* status, const uint32_t* list,
-                        const uint32_t* list_n) {
+                        int64_t* visited, cudaStream_t st, uint32_t* status) {
   if (!status) status = ix->status;
   if (k < 1 || k > 64) return fail(CG_ERR_INVALID, "k must be in [1, 64]");
   if (policy != 0 && policy != 1) return fail(CG_ERR_INVALID, "policy must be 0 (monotone) or 1 (density)");
@@ -1808,10 +1803,10 @@ cg_status knn_grow_pass(cg_index* ix, const double* q, int64_t nq, int k, int po
   ProfScope prof("knn_grow", st);
   if (ix->precision == CG_FP32_OFFSET)
     knn_grow_kernel<1><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
-                                             reinterpret_cast<long long*>(visited), status, list, list_n);
+                                             reinterpret_cast<long long*>(visited), status);
   else
     knn_grow_kernel<0><<<grid, 128, 0, st>>>(ix->view(), q, (uint32_t)nq, k, policy, idx, d2,
-                                             reinterpret_cast<long long*>(visited), status, list, list_n);
+                                             reinterpret_cast<long long*>(visited), status);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k-NN growth kernel");
