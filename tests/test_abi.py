@@ -53,3 +53,13 @@ def test_argument_errors_without_gpu():
     # NULL index
     assert lib.cg_index_free(None) == 1
     assert lib.cg_all_points_count(None, 1.0, 0, fake, None, None) == 1
+    # the one-call search into a buffer: NULL index, NULL outputs, a
+    # negative capacity, a NULL buffer with a positive capacity
+    tot = ctypes.c_int64(-1)
+    assert lib.cg_radius_search_into(None, fake, 1, 1.0, 0, fake, fake, 10, ctypes.byref(tot), None) == 1
+    assert lib.cg_radius_search_into(fake, fake, 1, 1.0, 0, None, fake, 10, ctypes.byref(tot), None) == 1
+    assert lib.cg_radius_search_into(fake, fake, 1, 1.0, 0, fake, fake, 10, None, None) == 1
+    assert lib.cg_radius_search_into(fake, fake, 1, 1.0, 0, fake, None, 10, ctypes.byref(tot), None) == 1
+    assert lib.cg_radius_search_into(fake, fake, 1, 1.0, 0, fake, fake, -1, ctypes.byref(tot), None) == 1
+    assert b"capacity" in lib.cg_last_error()
+    assert tot.value == -1  # untouched on an argument error
