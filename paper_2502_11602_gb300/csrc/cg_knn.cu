@@ -43,7 +43,7 @@ constexpr int LCAP = 128;          // per-warp candidate list
 constexpr int NB = 64;             // histogram buckets
 
 template <int PREC> struct KRec;
-template <> struct KRec<1> { using T = float4; static constexpr int KMAX = 4096; };
+template <> struct KRec<1> { using T = float4; };
 template <> struct KRec<0> { using T = double4_32a; static constexpr int KMAX = 2048; };
 
 __device__ __forceinline__ uint32_t krec_id(const float4& r) { return __float_as_uint(r.w); }
@@ -100,15 +100,10 @@ __device__ __forceinline__ KBound make_kbound(const Thresholds& thr) {
   return kb;
 }
 
-__device__ __forceinline__ float rec_u_k(const float4& q, const Tile& T, int a) {
-  float x = a == 0 ? q.x : (a == 1 ? q.y : q.z);
-  return __fmul_rn(__fadd_rn(x, T.D[a]), T.inv_sf[a]);
-}
 __device__ __forceinline__ float rec_u_k(const double4_32a& q, const Tile& T, int a) {
   double x = a == 0 ? q.x : (a == 1 ? q.y : q.z);
   return __fmul_rn(__double2float_rn(__dsub_rn(x, T.lo[a])), T.inv_sf[a]);
 }
-__device__ __forceinline__ float rec_abs_k(const float4& q, int a) { return fabsf(a == 0 ? q.x : (a == 1 ? q.y : q.z)); }
 __device__ __forceinline__ float rec_abs_k(const double4_32a&, int) { return 0.f; }
 
 // Certified lower bound on the squared distance from the query to any point
@@ -1614,7 +1609,7 @@ out:
 
 // Binary32 fast path (k <= 64): group boxes of radius 1 in three size
 // classes (staged boxes of <= 512, 1024 and 2048 candidates; list length
-// the class's largest k + 2: 10, 18, 34 or 66), then the bounded search of the queries
+// the class's largest k + 2: 4, 10, 18, 34 or 66), then the bounded search of the queries
 // left undecided.  bslot / br2 have room for every query; ctrs[4..6] are
 // the box launches' group counters, ctrs[9] the bounded list's length,
 // ctrs[0] the ring-by-ring list's.
@@ -1644,7 +1639,11 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
   } while (0)
   // warps per group: 1, 2, 4 for the three classes (their groups hold about
   // 1, 2.5 and 4 chunks of 32 queries), sharing the staged box
-  if (k <= 8) {
+  if (k <= 2) {
+    CG_K5(512, 4, 4, 1, 0u);
+    CG_K5(1024, 4, 4, 2, 1u);
+    CG_K5(2048, 4, 4, 4, 2u);
+  } else if (k <= 8) {
     CG_K5(512, 10, 4, 1, 0u);
     CG_K5(1024, 10, 4, 2, 1u);
     CG_K5(2048, 10, 4, 4, 2u);
