@@ -1609,7 +1609,7 @@ out:
 
 // Binary32 fast path (k <= 64): group boxes of radius 1 in three size
 // classes (staged boxes of <= 512, 1024 and 2048 candidates; list length
-// the class's largest k + 2: 4, 10, 18, 34 or 66), then the bounded search of the queries
+// the class's largest k + 2: 4, 6, 10, 18, 34 or 66), then the bounded search of the queries
 // left undecided.  bslot / br2 have room for every query; ctrs[4..6] are
 // the box launches' group counters, ctrs[9] the bounded list's length,
 // ctrs[0] the ring-by-ring list's.
@@ -1643,6 +1643,10 @@ cudaError_t launch_knn5(const IndexView& iv, const QuerySet& qs, const Threshold
     CG_K5(512, 4, 4, 1, 0u);
     CG_K5(1024, 4, 4, 2, 1u);
     CG_K5(2048, 4, 4, 4, 2u);
+  } else if (k <= 4) {
+    CG_K5(512, 6, 4, 1, 0u);
+    CG_K5(1024, 6, 4, 2, 1u);
+    CG_K5(2048, 6, 4, 4, 2u);
   } else if (k <= 8) {
     CG_K5(512, 10, 4, 1, 0u);
     CG_K5(1024, 10, 4, 2, 1u);

@@ -28,7 +28,7 @@ def _check(xyz, q, k, cell, cell_z=None, dim=2, flavor=cg.DENSE, prec=cg.FP32_OF
 
 
 @pytest.mark.parametrize("prec", [cg.FP32_OFFSET, cg.FP64])
-@pytest.mark.parametrize("k", [1, 2, 3, 8, 9, 16, 17, 32, 33, 64])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 9, 16, 17, 32, 33, 64])
 def test_small_als_tile_all_points(prec, k):
     xyz = cloudgen.als_uniform(60_000, extent=(75.0, 75.0))
     _check(xyz, None, k, 1.0, prec=prec)
